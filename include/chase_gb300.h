@@ -1,0 +1,188 @@
+/*
+ * chase_gb300.h -- C ABI of the GB300 (sm_103a) Chebyshev-filtered subspace
+ * iteration library.
+ *
+ * The library computes the nev lowest eigenpairs of a dense Hermitian (or real
+ * symmetric) matrix A of order n by the method of Di Napoli & Wu, "Estimating
+ * the condition number of Chebyshev filtered vectors with application to the
+ * ChASE library" (Algorithm 1): Chebyshev filter (Algorithm 4, per-column
+ * degrees, Section 2.3), orthonormalisation of [Y V] by CholeskyQR1 /
+ * CholeskyQR2 / shifted CholeskyQR2 chosen by the condition-number estimate of
+ * Eq. full-est (Algorithm 3), Householder QR as the fallback, Rayleigh-Ritz,
+ * residuals (eq. res) and locking.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major with a leading dimension (LAPACK layout):
+ *     element (i, j) of X lives at X[i + j*ldx].
+ *   - CHASE_R64 data are `double`; CHASE_C128 data are interleaved complex
+ *     doubles (`double _Complex` / `cuDoubleComplex`, 16 bytes, real first).
+ *   - Pointers named d* are DEVICE pointers (on the handle's device);
+ *     everything else is host memory.  The caller owns every buffer it passes
+ *     and keeps it alive for the duration of the call.  The handle owns its
+ *     workspace (device memory it allocates and grows on demand).
+ *   - A is read in full (both triangles); the caller guarantees A = A^H.
+ *   - All device work is ordered on the handle's CUDA stream; every entry point
+ *     returns after that work has completed (it synchronises the stream).
+ *   - Return value: CHASE_OK (0); a negative value -i means argument i (1-based,
+ *     in the order of the C prototype) is invalid and nothing was done;
+ *     positive values are the chase_status codes below.
+ *   - No entry point traps or aborts: device-side failures (a non-positive
+ *     Cholesky pivot, a non-finite value) are reported through status codes.
+ */
+#ifndef CHASE_GB300_H
+#define CHASE_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chase_ctx* chase_handle;
+
+typedef enum { CHASE_R64 = 0, CHASE_C128 = 1 } chase_dtype;
+
+/* Arithmetic of the filter's A*V products.  FP64 is exact double precision.
+ * The remaining steps (QR, Rayleigh-Ritz, residuals) are always FP64. */
+typedef enum { CHASE_FP64 = 0, CHASE_TF32 = 1, CHASE_BF16X3 = 2 } chase_precision;
+
+typedef enum {
+  CHASE_OK = 0,
+  CHASE_NOT_CONVERGED = 1,  /* max_iter reached; partial results returned */
+  CHASE_CHOL_FAILED = 2,    /* a forced Cholesky variant failed (chase_qr only) */
+  CHASE_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+  CHASE_ERR_OOM = 4,        /* workspace allocation failed */
+  CHASE_ERR_TIMEOUT = 5,    /* a bounded device wait gave up */
+  CHASE_ERR_NONFINITE = 6,  /* NaN/Inf met in the data */
+  CHASE_ERR_UNSUPPORTED = 7 /* option not available in this build */
+} chase_status;
+
+/* Variant codes of Algorithm 3 (also used by qr_force). */
+enum { CHASE_QR_AUTO = 0, CHASE_QR_CHOL1 = 1, CHASE_QR_CHOL2 = 2, CHASE_QR_SHIFTED = 3,
+       CHASE_QR_HOUSEHOLDER = 4 };
+
+typedef struct {
+  double tol;        /* residual threshold of eq. res (Section 2.4), default 1e-10 */
+  int max_iter;      /* outer iterations of Algorithm 1, default 25 */
+  int deg_init;      /* degree of every column in the first filter (Section 4.3: 20) */
+  int deg_min;       /* lower clamp of the optimised degrees, default 10 */
+  int deg_max;       /* upper clamp (Section 4.3: 36) */
+  int opt_degree;    /* 1: per-column degrees from the convergence ratio; 0: deg_init always */
+  double eta;        /* constant of Proposition th:2-2; 1 per Remark obs:2-1 */
+  double cond_hi;    /* Algorithm 3: shifted CholeskyQR2 above this estimate (1e8) */
+  double cond_lo;    /* Algorithm 3: CholeskyQR1 below this estimate (20) */
+  int qr_force;      /* CHASE_QR_AUTO or a forced variant */
+  chase_precision prec; /* filter arithmetic */
+  int reserved[8];
+} chase_config;
+
+/* Spectral information the filter needs (Algorithm 1, step "estimate lambda_1,
+ * lambda_ell and lambda_n"): lambda1 ~ lowest eigenvalue, lambda_ell ~ the
+ * ell-th eigenvalue, b_sup >= largest eigenvalue (must bound it from above). */
+typedef struct {
+  double lambda1, lambda_ell, b_sup;
+} chase_bounds;
+
+typedef struct {
+  int iterations;
+  int locked;
+  long long matvecs;       /* sum over iterations of the unlocked columns' degrees */
+  int n_chol1, n_chol2, n_shifted, n_hhqr; /* QR variant used per iteration */
+  int n_chol_failures;     /* Cholesky failures that triggered an escalation */
+  double t_total, t_filter, t_qr, t_rr, t_resid; /* seconds, CUDA-event timed */
+  double filter_flops;     /* algorithmic flops of the filter products */
+} chase_stats;
+
+/* Per-iteration record (the kind of data Figure 2 plots). */
+typedef struct {
+  int iteration, locked_before, locked_after, variant, chol_fail_info, deg_min, deg_max;
+  long long matvecs;
+  double log_cond_est, c, e, mu1, mu_ell;
+} chase_iter_log;
+
+/* Creates a handle bound to CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to order work on, or NULL for a new non-blocking stream owned
+ * by the handle.  Returns CHASE_ERR_CUDA if the device cannot be used. */
+int chase_create(chase_handle* h, int device, void* cuda_stream);
+
+/* Frees the handle's workspace and stream (if it owns one). */
+int chase_destroy(chase_handle h);
+
+/* Fills *cfg with the defaults listed above. */
+int chase_config_default(chase_config* cfg);
+
+/* Device workspace chase_solve needs for this problem shape (bytes). */
+int chase_workspace_bytes(chase_dtype dtype, int n, int nev, int nex, chase_precision prec,
+                          size_t* bytes);
+
+/*
+ * chase_solve -- Algorithm 1.
+ *   n         matrix order (>= 1);  dA: n x n device matrix, lda >= n.
+ *   nev, nex  wanted pairs and extra search vectors; ell = nev + nex <= n.
+ *   cfg       options (NULL: defaults);  bounds: spectral estimates (required).
+ *   dV        device n x ell block, ldv >= n.  On entry: the start block V0 of
+ *             Algorithm 1 (random or a warm start; need not be orthonormal).
+ *             On exit: columns 0..nev-1 hold the eigenvectors Y in ascending
+ *             eigenvalue order, the other columns the remaining search block.
+ *   evals     host, nev doubles: eigenvalues ascending.
+ *   resid     host, nev doubles: residual norms ||A y - lambda y||_2 (eq. res).
+ *   stats     host, optional (may be NULL).
+ *   log, log_cap  host array of per-iteration records (may be NULL / 0).
+ * Returns CHASE_OK when all nev pairs met tol, CHASE_NOT_CONVERGED after
+ * max_iter iterations (results are the current approximations), or an error.
+ */
+int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda, int nev,
+                int nex, const chase_config* cfg, const chase_bounds* bounds, void* dV, int ldv,
+                double* evals, double* resid, chase_stats* stats, chase_iter_log* log,
+                int log_cap);
+
+/*
+ * chase_filter -- Algorithm 4 with per-column degrees (Section 2.3):
+ *   dVout[:, a] = p_{m_a}(A) dV[:, a],  p_m(x) = C_m((x - c)/e) / C_m((lambda1 - c)/e),
+ * computed by the scaled three-term recurrence.  The damped interval is
+ * [c - e, c + e] (e > 0) and lambda1 < c - e.
+ *   degrees   host, ncols ints, ascending, each >= 0 (0 copies the column).
+ *   dV        device n x ncols input (not modified); dVout device n x ncols
+ *             output (may equal dV).
+ *   prec      CHASE_FP64 (others: CHASE_ERR_UNSUPPORTED when not built).
+ */
+int chase_filter(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda, int ncols,
+                 const void* dV, int ldv, const int* degrees, double c, double e, double lambda1,
+                 chase_precision prec, void* dVout, int ldvout);
+
+/*
+ * chase_qr -- Algorithm 3 on the device block dX (n x ncols, in place):
+ *   qr_force = CHASE_QR_AUTO picks by est_cond (shifted CholeskyQR2 if
+ *   est_cond > 1e8, CholeskyQR1 if < 20, else CholeskyQR2; a failing
+ *   Cholesky escalates to the shifted branch and then to Householder QR);
+ *   a forced Cholesky variant that fails returns CHASE_CHOL_FAILED with dX
+ *   unchanged.  On success dX holds an orthonormal basis Q of its column
+ *   space with X = Q R.
+ *   variant_used, chol_info: host outputs (may be NULL).
+ */
+int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int ldx,
+             double est_cond, int qr_force, int* variant_used, int* chol_info);
+
+/*
+ * chase_cond_est -- the estimate of Eq. full-est (Corollary cr:3-1):
+ *   kappa_est = eta |rho_{k+1}|^{m_{k+1}} |rho_1|^{m_ell - m_{k+1}},
+ * |rho(x)| = |t| + sqrt(t^2 - 1), t = (x - c)/e (1 inside the damped interval).
+ *   ell, nlocked    block width and k;  ritz: host, ell Ritz values (the one at
+ *   index nlocked belongs to the first unlocked column);  degrees: host, ell
+ *   degrees (degrees[nlocked] = m_{k+1}, degrees[ell-1] = m_ell);
+ *   lambda1: lowest-eigenvalue estimate (gives rho_1).
+ *   est: host output kappa_est;  log_est (may be NULL): its natural log, finite
+ *   even when kappa_est overflows.
+ * Host arithmetic only; no handle needed.
+ */
+int chase_cond_est(int ell, int nlocked, const double* ritz, const int* degrees, double lambda1,
+                   double c, double e, double eta, double* est, double* log_est);
+
+/* Static description of a status code. */
+const char* chase_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHASE_GB300_H */

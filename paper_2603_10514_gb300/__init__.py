@@ -1,0 +1,237 @@
+"""Python binding of the GB300 Chebyshev-filtered subspace iteration library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libchase_gb300.so`` behind the C ABI of ``include/chase_gb300.h``.
+There is no CPU fallback; if the library has not been built (``build()``) or no
+CUDA device is present, the calls raise.
+
+Device buffers are torch tensors on the handle's device in column-major layout
+(strides (1, ld)); host arrays are numpy.  The entry points keep the C names:
+``chase_solve``, ``chase_filter``, ``chase_qr``, ``chase_cond_est``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchase_gb300.so")
+
+CHASE_R64, CHASE_C128 = 0, 1
+CHASE_FP64, CHASE_TF32, CHASE_BF16X3 = 0, 1, 2
+CHASE_OK, CHASE_NOT_CONVERGED, CHASE_CHOL_FAILED = 0, 1, 2
+CHASE_ERR_CUDA, CHASE_ERR_OOM, CHASE_ERR_TIMEOUT, CHASE_ERR_NONFINITE, CHASE_ERR_UNSUPPORTED = 3, 4, 5, 6, 7
+QR_VARIANTS = {1: "cholqr1", 2: "cholqr2", 3: "shifted_cholqr2", 4: "householder"}
+
+EXPORTED = ["chase_create", "chase_destroy", "chase_config_default", "chase_workspace_bytes",
+            "chase_solve", "chase_filter", "chase_qr", "chase_cond_est", "chase_status_string"]
+
+
+class ChaseError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %d (%s)" % (where, code, status_string(code)))
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("deg_init", ctypes.c_int),
+                ("deg_min", ctypes.c_int), ("deg_max", ctypes.c_int), ("opt_degree", ctypes.c_int),
+                ("eta", ctypes.c_double), ("cond_hi", ctypes.c_double), ("cond_lo", ctypes.c_double),
+                ("qr_force", ctypes.c_int), ("prec", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class Bounds(ctypes.Structure):
+    _fields_ = [("lambda1", ctypes.c_double), ("lambda_ell", ctypes.c_double), ("b_sup", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("locked", ctypes.c_int), ("matvecs", ctypes.c_longlong),
+                ("n_chol1", ctypes.c_int), ("n_chol2", ctypes.c_int), ("n_shifted", ctypes.c_int),
+                ("n_hhqr", ctypes.c_int), ("n_chol_failures", ctypes.c_int),
+                ("t_total", ctypes.c_double), ("t_filter", ctypes.c_double), ("t_qr", ctypes.c_double),
+                ("t_rr", ctypes.c_double), ("t_resid", ctypes.c_double), ("filter_flops", ctypes.c_double)]
+
+
+class IterLog(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int), ("locked_before", ctypes.c_int),
+                ("locked_after", ctypes.c_int), ("variant", ctypes.c_int),
+                ("chol_fail_info", ctypes.c_int), ("deg_min", ctypes.c_int), ("deg_max", ctypes.c_int),
+                ("matvecs", ctypes.c_longlong), ("log_cond_est", ctypes.c_double),
+                ("c", ctypes.c_double), ("e", ctypes.c_double), ("mu1", ctypes.c_double),
+                ("mu_ell", ctypes.c_double)]
+
+
+_lib = None
+
+
+def build(verbose=False):
+    """Compile the CUDA library for sm_103a (see _buildlib.py)."""
+    from . import _buildlib
+    return _buildlib.build(verbose=verbose)
+
+
+def lib():
+    """Load ``libchase_gb300.so``; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libchase_gb300.so is not built: run paper_2603_10514_gb300.build() "
+                               "(nvcc, sm_103a) first; there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.chase_create.argtypes = [ctypes.POINTER(P), i, P]
+        L.chase_destroy.argtypes = [P]
+        L.chase_config_default.argtypes = [ctypes.POINTER(Config)]
+        L.chase_workspace_bytes.argtypes = [i, i, i, i, i, ctypes.POINTER(ctypes.c_size_t)]
+        L.chase_solve.argtypes = [P, i, i, P, i, i, i, ctypes.POINTER(Config), ctypes.POINTER(Bounds),
+                                  P, i, P, P, ctypes.POINTER(Stats), P, i]
+        L.chase_filter.argtypes = [P, i, i, P, i, i, P, i, P, d, d, d, i, P, i]
+        L.chase_qr.argtypes = [P, i, i, i, P, i, d, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.chase_cond_est.argtypes = [i, i, P, P, d, d, d, d, ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.chase_status_string.argtypes = [i]
+        L.chase_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(code):
+    try:
+        return lib().chase_status_string(int(code)).decode()
+    except Exception:  # library missing: still format the error
+        return "status %d" % code
+
+
+def config_default(**kw):
+    cfg = Config()
+    rc = lib().chase_config_default(ctypes.byref(cfg))
+    if rc:
+        raise ChaseError(rc, "chase_config_default")
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return CHASE_R64
+    if t.dtype == torch.complex128:
+        return CHASE_C128
+    raise TypeError("tensor dtype must be float64 or complex128, got %s" % t.dtype)
+
+
+def _ld(t, name):
+    """Leading dimension of a column-major 2-D CUDA tensor."""
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dim() == 2 and t.numel() == 0:
+        return max(1, t.shape[0])
+    if t.dim() != 2 or t.stride(0) != 1 or t.stride(1) < max(1, t.shape[0]):
+        raise ValueError("%s must be column-major (strides (1, ld)), got strides %s" % (name, t.stride()))
+    return t.stride(1)
+
+
+def colmajor(t):
+    """A column-major copy (strides (1, rows)) of a 2-D tensor."""
+    return t.mT.contiguous().mT
+
+
+class Handle:
+    """Owns a chase_handle: a device, a CUDA stream and the device workspace."""
+
+    def __init__(self, device=0, stream=None):
+        self._h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream) if stream is not None else None
+        rc = lib().chase_create(ctypes.byref(self._h), int(device), s)
+        if rc:
+            raise ChaseError(rc, "chase_create")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().chase_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ptr(self):
+        return self._h
+
+
+def chase_solve(h, A, V, nev, nex, bounds, cfg=None, log_cap=64, check=True):
+    """Algorithm 1.  A: (n, n) column-major CUDA tensor; V: (n, nev+nex) column-major CUDA
+    tensor holding V0 on entry and the final block (eigenvectors first) on exit.
+    bounds = (lambda1, lambda_ell, b_sup).  Returns (status, evals, resid, stats dict, logs)."""
+    n = A.shape[0]
+    dt = _dtype_code(A)
+    if _dtype_code(V) != dt:
+        raise TypeError("A and V must have the same dtype")
+    lda, ldv = _ld(A, "A"), _ld(V, "V")
+    if cfg is None:
+        cfg = config_default()
+    b = Bounds(*[float(x) for x in bounds])
+    evals = np.zeros(nev)
+    resid = np.zeros(nev)
+    st = Stats()
+    logs = (IterLog * max(1, log_cap))()
+    rc = lib().chase_solve(h.ptr, dt, n, ctypes.c_void_p(A.data_ptr()), lda, nev, nex, ctypes.byref(cfg),
+                           ctypes.byref(b), ctypes.c_void_p(V.data_ptr()), ldv,
+                           evals.ctypes.data_as(ctypes.c_void_p), resid.ctypes.data_as(ctypes.c_void_p),
+                           ctypes.byref(st), ctypes.cast(logs, ctypes.c_void_p), log_cap)
+    if check and rc not in (CHASE_OK, CHASE_NOT_CONVERGED):
+        raise ChaseError(rc, "chase_solve")
+    stats = {f: getattr(st, f) for f, _ in Stats._fields_}
+    lg = [{f: getattr(logs[j], f) for f, _ in IterLog._fields_} for j in range(min(st.iterations, log_cap))]
+    return rc, evals, resid, stats, lg
+
+
+def chase_filter(h, A, V, degrees, c, e, lambda1, out=None, prec=CHASE_FP64):
+    """Algorithm 4 with per-column degrees; returns the filtered block (new tensor unless out)."""
+    import torch
+    n, ncols = V.shape
+    dt = _dtype_code(A)
+    lda, ldv = _ld(A, "A"), _ld(V, "V")
+    if out is None:
+        out = colmajor(torch.empty_like(V))
+    ldo = _ld(out, "out")
+    deg = np.ascontiguousarray(degrees, dtype=np.int32)
+    rc = lib().chase_filter(h.ptr, dt, n, ctypes.c_void_p(A.data_ptr()), lda, ncols,
+                            ctypes.c_void_p(V.data_ptr()), ldv, deg.ctypes.data_as(ctypes.c_void_p),
+                            float(c), float(e), float(lambda1), int(prec),
+                            ctypes.c_void_p(out.data_ptr()), ldo)
+    if rc:
+        raise ChaseError(rc, "chase_filter")
+    return out
+
+
+def chase_qr(h, X, est_cond, qr_force=0, check=True):
+    """Algorithm 3 in place on the CUDA tensor X.  Returns (status, variant, chol_info)."""
+    n, l = X.shape
+    dt = _dtype_code(X)
+    ldx = _ld(X, "X")
+    v, info = ctypes.c_int(0), ctypes.c_int(0)
+    rc = lib().chase_qr(h.ptr, dt, n, l, ctypes.c_void_p(X.data_ptr()), ldx, float(est_cond),
+                        int(qr_force), ctypes.byref(v), ctypes.byref(info))
+    if check and rc not in (CHASE_OK, CHASE_CHOL_FAILED):
+        raise ChaseError(rc, "chase_qr")
+    return rc, v.value, info.value
+
+
+def chase_cond_est(ritz, degrees, nlocked, lambda1, c, e, eta=1.0):
+    """Eq. full-est.  Returns (est, log_est)."""
+    r = np.ascontiguousarray(ritz, dtype=np.float64)
+    d = np.ascontiguousarray(degrees, dtype=np.int32)
+    est, lest = ctypes.c_double(), ctypes.c_double()
+    rc = lib().chase_cond_est(len(r), int(nlocked), r.ctypes.data_as(ctypes.c_void_p),
+                              d.ctypes.data_as(ctypes.c_void_p), float(lambda1), float(c), float(e),
+                              float(eta), ctypes.byref(est), ctypes.byref(lest))
+    if rc:
+        raise ChaseError(rc, "chase_cond_est")
+    return est.value, lest.value

@@ -1,0 +1,94 @@
+// common.cuh -- scalar types, error handling and small device helpers shared by
+// the GB300 kernels of the Chebyshev-filtered subspace iteration library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+
+namespace chase {
+
+// Interleaved complex double (same bytes as double _Complex / cuDoubleComplex).
+struct __align__(16) z64 {
+  double x, y;
+};
+
+__host__ __device__ inline z64 mkz(double a, double b) { return z64{a, b}; }
+
+// ---- scalar traits ---------------------------------------------------------
+template <class T> struct Sc;
+
+template <> struct Sc<double> {
+  static constexpr bool cplx = false;
+  __host__ __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double one() { return 1.0; }
+  __host__ __device__ static double conj(double a) { return a; }
+  __host__ __device__ static double re(double a) { return a; }
+  __host__ __device__ static double abs2(double a) { return a * a; }
+  __host__ __device__ static double from_re(double a) { return a; }
+  // acc += a * b
+  __device__ static void fma(double& acc, double a, double b) { acc = ::fma(a, b, acc); }
+  // acc += conj(a) * b
+  __device__ static void fmac(double& acc, double a, double b) { acc = ::fma(a, b, acc); }
+  __host__ __device__ static double mul(double a, double b) { return a * b; }
+  __host__ __device__ static double add(double a, double b) { return a + b; }
+  __host__ __device__ static double sub(double a, double b) { return a - b; }
+  __host__ __device__ static double scale(double a, double s) { return a * s; }
+  __device__ static bool finite(double a) { return isfinite(a); }
+};
+
+template <> struct Sc<z64> {
+  static constexpr bool cplx = true;
+  __host__ __device__ static z64 zero() { return z64{0.0, 0.0}; }
+  __host__ __device__ static z64 one() { return z64{1.0, 0.0}; }
+  __host__ __device__ static z64 conj(z64 a) { return z64{a.x, -a.y}; }
+  __host__ __device__ static double re(z64 a) { return a.x; }
+  __host__ __device__ static double abs2(z64 a) { return a.x * a.x + a.y * a.y; }
+  __host__ __device__ static z64 from_re(double a) { return z64{a, 0.0}; }
+  __device__ static void fma(z64& acc, z64 a, z64 b) {
+    acc.x = ::fma(a.x, b.x, acc.x);
+    acc.x = ::fma(-a.y, b.y, acc.x);
+    acc.y = ::fma(a.x, b.y, acc.y);
+    acc.y = ::fma(a.y, b.x, acc.y);
+  }
+  __device__ static void fmac(z64& acc, z64 a, z64 b) {  // conj(a) * b
+    acc.x = ::fma(a.x, b.x, acc.x);
+    acc.x = ::fma(a.y, b.y, acc.x);
+    acc.y = ::fma(a.x, b.y, acc.y);
+    acc.y = ::fma(-a.y, b.x, acc.y);
+  }
+  __host__ __device__ static z64 mul(z64 a, z64 b) {
+    return z64{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+  }
+  __host__ __device__ static z64 add(z64 a, z64 b) { return z64{a.x + b.x, a.y + b.y}; }
+  __host__ __device__ static z64 sub(z64 a, z64 b) { return z64{a.x - b.x, a.y - b.y}; }
+  __host__ __device__ static z64 scale(z64 a, double s) { return z64{a.x * s, a.y * s}; }
+  __device__ static bool finite(z64 a) { return isfinite(a.x) && isfinite(a.y); }
+};
+
+// ---- launch helpers --------------------------------------------------------
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Device status word written by kernels that can fail without trapping.
+struct DevStatus {
+  int chol_info;    // first non-positive pivot + 1 (0 = success)
+  int nonfinite;    // a NaN/Inf was met
+  int timeout;      // a bounded wait gave up
+  int pad;
+};
+
+}  // namespace chase
+
+#define CHASE_CUDA_TRY(expr)                         \
+  do {                                               \
+    cudaError_t _e = (expr);                         \
+    if (_e != cudaSuccess) return ::chase::fail_cuda(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+namespace chase {
+int fail_cuda(cudaError_t e, const char* what, const char* file, int line);
+}

@@ -1,0 +1,68 @@
+// kernels.h -- internal launchers of the GB300 kernels (not part of the C ABI).
+// Every launcher enqueues work on `st` and returns 0 or a chase_status code.
+#pragma once
+
+#include "common.cuh"
+
+namespace chase {
+
+// Device scratch memory handed to a launcher (split-K partial sums etc.).
+struct Scratch {
+  void* ptr;
+  size_t bytes;
+};
+
+// C = alpha * op(A) B + beta * X + gamma * Y  (op = identity or ^H); see gemm_fp64.cu.
+// upper_only: only C[i, j] with i <= j is needed (Hermitian results).
+// tri_b: B is upper triangular (entries below its diagonal are zero and skipped).
+template <class T>
+int gemm(cudaStream_t st, bool transA, int M, int N, int K, const T* A, int lda, const T* B,
+         int ldb, T* C, int ldc, double alpha, double beta, const T* X, int ldx, double gamma,
+         const T* Y, int ldy, Scratch scratch, bool upper_only, bool tri_b, int* launches);
+
+// ---- dense small-matrix kernels (chol_trsm.cu) ----------------------------
+// Upper Cholesky of G in place; info (first failing pivot + 1) goes to dst->chol_info.
+// shift_factor > 0 first adds s = shift_factor * trace(G) to the diagonal (the shifted
+// CholeskyQR step: trace(X^H X) = ||X||_F^2).
+template <class T>
+int potrf_upper(cudaStream_t st, int n, T* G, int ldg, double shift_factor, DevStatus* dst,
+                int* launches);
+// Rinv = R^{-1} for upper-triangular R (zero strict lower part written).
+template <class T>
+int trtri_upper(cudaStream_t st, int n, const T* R, int ldr, T* Rinv, int ldri, int* launches);
+
+// ---- Householder QR with explicit thin Q (householder.cu) -----------------
+template <class T>
+int householder_qr(cudaStream_t st, int n, int l, T* X, int ldx, T* Vh, int ldv, double* dnorm,
+                   int* launches);
+
+// ---- parallel cyclic Jacobi eigensolver (jacobi.cu) ------------------------
+// Diagonalises the Hermitian H (l x l, overwritten).  Eigenvalues (ascending)
+// go to dw (device) and eigenvectors to W.  Returns sweeps used through *sweeps.
+template <class T>
+int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw, void* work,
+               size_t work_bytes, int max_sweeps, int* sweeps, int* launches);
+
+// ---- streaming kernels (vec.cu) --------------------------------------------
+template <class T>
+int herm_fill_lower(cudaStream_t st, int n, T* G, int ldg, int* launches);
+// r_a = || AV[:,a] - theta_a V[:,a] || / || V[:,a] ||
+template <class T>
+int resid_norms(cudaStream_t st, int n, int ncols, const T* AV, int ldav, const T* V, int ldv,
+                const double* dtheta, double* dres, int* launches);
+template <class T>
+int copy_cols(cudaStream_t st, int n, int ncols, const T* src, int lds, T* dst, int ldd,
+              int* launches);
+// dst[:, a] = src[:, perm[a]]  (dperm on device)
+template <class T>
+int gather_cols(cudaStream_t st, int n, int ncols, const T* src, int lds, const int* dperm, T* dst,
+                int ldd, int* launches);
+// dst[:, a] = src_{sel[a]}[:, a] with sel[a] in {0,1}: picks each column from one of two buffers
+template <class T>
+int select_cols(cudaStream_t st, int n, int ncols, const T* src0, const T* src1, int lds,
+                const int* dsel, T* dst, int ldd, int* launches);
+template <class T>
+int nonfinite_check(cudaStream_t st, int n, int ncols, const T* X, int ldx, DevStatus* dst,
+                    int* launches);
+
+}  // namespace chase

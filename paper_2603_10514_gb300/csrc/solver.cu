@@ -1,0 +1,697 @@
+// solver.cu -- host driver of Algorithm 1 (ChASE) on one GB300 and the C ABI
+// declared in include/chase_gb300.h.
+//
+// All device work of a call is ordered on the handle's stream.  Host <-> device
+// traffic per outer iteration is small and explicit: the Cholesky info word
+// after each factorisation (Algorithm 2's "if info != 0"), and the Ritz values
+// and residuals after Rayleigh-Ritz (needed for locking and for the next
+// degrees).  A stays resident; the search block lives in handle workspace.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "../../include/chase_gb300.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace chase {
+
+int fail_cuda(cudaError_t e, const char* what, const char* file, int line) {
+  if (getenv("CHASE_DEBUG")) fprintf(stderr, "chase: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+  (void)what; (void)file; (void)line; (void)e;
+  return CHASE_ERR_CUDA;
+}
+
+}  // namespace chase
+
+using namespace chase;
+
+struct chase_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* ws = nullptr;  // workspace
+  size_t ws_bytes = 0;
+  DevStatus* dstat = nullptr;  // device status word
+  DevStatus* hstat = nullptr;  // pinned host mirror
+  double* hbuf = nullptr;      // pinned host staging (small vectors)
+  size_t hbuf_bytes = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int launches = 0;
+};
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(128) << 20;  // split-K partial sums
+constexpr double kU = 1.1102230246251565e-16;        // 2^-53
+
+#define TRY(x)                    \
+  do {                            \
+    int _rc = (x);                \
+    if (_rc) return _rc;          \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int ensure_ws(chase_ctx* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return 0;
+  if (h->ws) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return CHASE_ERR_OOM;
+  }
+  h->ws_bytes = bytes;
+  return 0;
+}
+
+int ensure_hbuf(chase_ctx* h, size_t bytes) {
+  if (bytes <= h->hbuf_bytes) return 0;
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  h->hbuf = nullptr;
+  h->hbuf_bytes = 0;
+  if (cudaMallocHost((void**)&h->hbuf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return CHASE_ERR_OOM;
+  }
+  h->hbuf_bytes = bytes;
+  return 0;
+}
+
+// Workspace carve-up for a problem of order n with block width l.
+struct Layout {
+  size_t V, P, AQ, T2, Xs, G, Ri, H, Wm, jac, dw, dres, scratch, total;
+};
+
+template <class T>
+Layout layout_for(int n, int l) {
+  Layout L{};
+  size_t off = 0;
+  const size_t blk = align256(sizeof(T) * (size_t)n * l);
+  const size_t sq = align256(sizeof(T) * (size_t)l * l);
+  L.V = off; off += blk;
+  L.P = off; off += blk;
+  L.AQ = off; off += blk;
+  L.T2 = off; off += blk;
+  L.Xs = off; off += blk;
+  L.G = off; off += sq;
+  L.Ri = off; off += sq;
+  L.H = off; off += sq;
+  L.Wm = off; off += sq;
+  L.jac = off; off += sq + align256(64 * (size_t)(l + 2)) + 1024;
+  L.dw = off; off += align256(sizeof(double) * (size_t)l);
+  L.dres = off; off += align256(sizeof(double) * (size_t)l);
+  L.scratch = off; off += kScratchBytes;
+  L.total = off;
+  return L;
+}
+
+double elapsed_s(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms * 1e-3;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 4 on columns [0, ncols) of V (in place), partner buffer P (ld ldp).
+// degrees ascending.  Column a ends at step m_a; columns with odd m_a finish in
+// P and are copied back at the end (runs of equal degree are contiguous).
+// ---------------------------------------------------------------------------
+template <class T>
+int filter_inplace(chase_ctx* h, int n, const T* A, int lda, int ncols, T* V, int ldv, T* P,
+                   int ldp, const int* deg, double c, double e, double lambda1, Scratch scr,
+                   double* flops) {
+  cudaStream_t st = h->stream;
+  if (ncols <= 0) return 0;
+  const int mmax = deg[ncols - 1];
+  const double sigma1 = e / (lambda1 - c);
+  double sigma = sigma1;
+  int first = 0;
+  const double per_col = (Sc<T>::cplx ? 8.0 : 2.0) * (double)n * (double)n;
+  for (int step = 1; step <= mmax; ++step) {
+    while (first < ncols && deg[first] < step) ++first;
+    const int act = ncols - first;
+    T* in = (step % 2 == 1) ? V : P;   // holds V_{step-1}
+    T* out = (step % 2 == 1) ? P : V;  // holds V_{step-2}, receives V_step
+    const int ldi = (step % 2 == 1) ? ldv : ldp;
+    const int ldo = (step % 2 == 1) ? ldp : ldv;
+    double alpha, beta, gamma;
+    if (step == 1) {
+      alpha = sigma1 / e;
+      beta = -alpha * c;
+      gamma = 0.0;
+    } else {
+      const double sn = 1.0 / (2.0 / sigma1 - sigma);
+      alpha = 2.0 * sn / e;
+      beta = -alpha * c;
+      gamma = -sigma * sn;
+      sigma = sn;
+    }
+    TRY(gemm<T>(st, false, n, act, n, A, lda, in + (size_t)first * ldi, ldi,
+                out + (size_t)first * ldo, ldo, alpha, beta, in + (size_t)first * ldi, ldi, gamma,
+                out + (size_t)first * ldo, ldo, scr, false, false, &h->launches));
+    if (flops) *flops += per_col * act;
+  }
+  // copy back the columns whose final result sits in P (odd degree)
+  int a = 0;
+  while (a < ncols) {
+    int b = a;
+    while (b < ncols && deg[b] == deg[a]) ++b;
+    if (deg[a] % 2 == 1)
+      TRY(copy_cols<T>(st, n, b - a, P + (size_t)a * ldp, ldp, V + (size_t)a * ldv, ldv, &h->launches));
+    a = b;
+  }
+  return 0;
+}
+
+// One CholeskyQR pass (Algorithm 2 body): X <- X R^{-1} with R = chol(X^H X [+ sI]).
+// Result lands in X (via Xtmp).  Returns 0, CHASE_CHOL_FAILED (info in *info) or an error.
+template <class T>
+int cholqr_pass(chase_ctx* h, int n, int l, T* X, int ldx, T* Xtmp, T* G, T* Ri, double shift_factor,
+                Scratch scr, int* info) {
+  cudaStream_t st = h->stream;
+  TRY(gemm<T>(st, true, l, l, n, X, ldx, X, ldx, G, l, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, scr,
+              true, false, &h->launches));
+  CHASE_CUDA_TRY(cudaMemsetAsync(&h->dstat->chol_info, 0, sizeof(int), st));
+  TRY(potrf_upper<T>(st, l, G, l, shift_factor, h->dstat, &h->launches));
+  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  *info = h->hstat->chol_info;
+  if (*info) return CHASE_CHOL_FAILED;
+  TRY(trtri_upper<T>(st, l, G, l, Ri, l, &h->launches));
+  TRY(gemm<T>(st, false, n, l, l, X, ldx, Ri, l, Xtmp, n, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
+              scr, false, true, &h->launches));
+  TRY(copy_cols<T>(st, n, l, Xtmp, n, X, ldx, &h->launches));
+  return 0;
+}
+
+// Algorithm 3 with escalation.  X (n x l, ld ldx) in place.  Workspace: Xtmp, Xsave (n x l, ld n),
+// G, Ri (l x l).  variant in/out: requested (0 = by log_est) -> used.
+template <class T>
+int qr_dynamic(chase_ctx* h, int n, int l, T* X, int ldx, double log_est, double cond_hi,
+               double cond_lo, int force, T* Xtmp, T* Xsave, T* G, T* Ri, Scratch scr,
+               int* variant_used, int* first_fail_info) {
+  cudaStream_t st = h->stream;
+  int variant = force;
+  if (force == 0) {
+    if (log_est > std::log(cond_hi)) variant = 3;
+    else if (log_est < std::log(cond_lo)) variant = 1;
+    else variant = 2;
+  }
+  if (first_fail_info) *first_fail_info = 0;
+  const bool need_save = (variant != 4);
+  if (need_save) TRY(copy_cols<T>(st, n, l, X, ldx, Xsave, n, &h->launches));
+  const double shift_factor = 11.0 * ((double)n * l + (double)l * (l + 1)) * kU;
+  for (;;) {
+    int info = 0, rc = 0;
+    if (variant == 1 || variant == 2) {
+      for (int p = 0; p < variant && rc == 0; ++p)
+        rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, 0.0, scr, &info);
+    } else if (variant == 3) {
+      rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, shift_factor, scr, &info);
+      for (int p = 0; p < 2 && rc == 0; ++p)
+        rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, 0.0, scr, &info);
+    } else {
+      TRY(householder_qr<T>(st, n, l, X, ldx, Xtmp, n, nullptr, &h->launches));
+      break;
+    }
+    if (rc == 0) break;
+    if (rc != CHASE_CHOL_FAILED) return rc;
+    if (first_fail_info && !*first_fail_info) *first_fail_info = info;
+    if (force != 0) {  // forced variant: report, restore the input
+      TRY(copy_cols<T>(st, n, l, Xsave, n, X, ldx, &h->launches));
+      CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+      if (variant_used) *variant_used = variant;
+      return CHASE_CHOL_FAILED;
+    }
+    TRY(copy_cols<T>(st, n, l, Xsave, n, X, ldx, &h->launches));
+    variant = (variant < 3) ? 3 : 4;
+  }
+  if (variant_used) *variant_used = variant;
+  return 0;
+}
+
+double abs_rho(double x, double c, double e) {
+  double t = std::fabs((x - c) / e);
+  if (t <= 1.0) return 1.0;
+  return t + std::sqrt(t * t - 1.0);
+}
+
+double log_cond_est(double theta_k1, int m_k1, int m_ell, double lambda1, double c, double e,
+                    double eta) {
+  return std::log(eta) + (double)m_k1 * std::log(abs_rho(theta_k1, c, e)) +
+         (double)(m_ell - m_k1) * std::log(abs_rho(lambda1, c, e));
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1
+// ---------------------------------------------------------------------------
+template <class T>
+int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const chase_config& cfg,
+               const chase_bounds& bd, T* dV, int ldv, double* evals, double* resid,
+               chase_stats* stats, chase_iter_log* logs, int log_cap) {
+  cudaStream_t st = h->stream;
+  const int l = nev + nex;
+  const Layout L = layout_for<T>(n, l);
+  TRY(ensure_ws(h, L.total));
+  TRY(ensure_hbuf(h, sizeof(double) * 4 * (size_t)l + 4096));
+  char* base = (char*)h->ws;
+  T* V = (T*)(base + L.V);
+  T* P = (T*)(base + L.P);
+  T* AQ = (T*)(base + L.AQ);
+  T* T2 = (T*)(base + L.T2);
+  T* Xs = (T*)(base + L.Xs);
+  T* G = (T*)(base + L.G);
+  T* Ri = (T*)(base + L.Ri);
+  T* H = (T*)(base + L.H);
+  T* Wm = (T*)(base + L.Wm);
+  void* jac = base + L.jac;
+  const size_t jac_bytes = L.dw - L.jac;
+  double* dw = (double*)(base + L.dw);
+  double* dres = (double*)(base + L.dres);
+  Scratch scr{base + L.scratch, kScratchBytes};
+  double* hw = h->hbuf;        // l Ritz values
+  double* hr = h->hbuf + l;    // l residuals
+
+  chase_stats S{};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto phase_begin = [&]() { cudaEventRecord(e0, st); };
+  auto phase_end = [&](double& acc) {
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    acc += elapsed_s(e0, e1);
+  };
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, st);
+
+  int rc = 0;
+  std::vector<int> deg(l, cfg.deg_init);
+  std::vector<double> ritz(l, bd.lambda1), res(l, 1.0);
+  std::vector<int> perm(l);
+  double mu1 = bd.lambda1, mu_ell = bd.lambda_ell;
+  const double bsup = bd.b_sup;
+  int k = 0, it = 0, status = CHASE_NOT_CONVERGED;
+  long long matvecs = 0;
+
+  CHASE_CUDA_TRY(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), st));
+  TRY(copy_cols<T>(st, n, l, dV, ldv, V, n, &h->launches));
+  TRY(nonfinite_check<T>(st, n, n, A, lda, h->dstat, &h->launches));
+  TRY(nonfinite_check<T>(st, n, l, V, n, h->dstat, &h->launches));
+  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h->hstat->nonfinite) rc = CHASE_ERR_NONFINITE;
+
+  // step 0: orthonormalise V0 (CholeskyQR2; Householder if forced or on failure)
+  if (!rc) {
+    phase_begin();
+    int v0 = 0, fi = 0;
+    rc = qr_dynamic<T>(h, n, l, V, n, std::log(100.0), cfg.cond_hi, cfg.cond_lo,
+                       cfg.qr_force == 4 ? 4 : 0, P, Xs, G, Ri, scr, &v0, &fi);
+    phase_end(S.t_qr);
+  }
+
+  for (it = 0; !rc && it < cfg.max_iter; ++it) {
+    const double c = 0.5 * (bsup + mu_ell), e = 0.5 * (bsup - mu_ell);
+    const int nu = l - k;
+    // --- filter ---
+    phase_begin();
+    rc = filter_inplace<T>(h, n, A, lda, nu, V + (size_t)k * n, n, P, n, deg.data() + k, c, e, mu1,
+                           scr, &S.filter_flops);
+    phase_end(S.t_filter);
+    if (rc) break;
+    for (int a = k; a < l; ++a) matvecs += deg[a];
+    // --- condition estimate (Eq. full-est) and QR (Algorithm 3) ---
+    const double theta_k1 = (it == 0) ? mu1 : ritz[k];
+    const double lest = log_cond_est(theta_k1, deg[k], deg[l - 1], mu1, c, e, cfg.eta);
+    phase_begin();
+    if (k > 0) rc = copy_cols<T>(st, n, k, V, n, T2, n, &h->launches);
+    int variant = 0, fi = 0;
+    if (!rc) rc = qr_dynamic<T>(h, n, l, V, n, lest, cfg.cond_hi, cfg.cond_lo, cfg.qr_force, P, Xs,
+                                G, Ri, scr, &variant, &fi);
+    if (!rc && k > 0) rc = copy_cols<T>(st, n, k, T2, n, V, n, &h->launches);
+    phase_end(S.t_qr);
+    if (rc) break;
+    if (variant == 1) ++S.n_chol1;
+    else if (variant == 2) ++S.n_chol2;
+    else if (variant == 3) ++S.n_shifted;
+    else ++S.n_hhqr;
+    if (fi) ++S.n_chol_failures;
+    // --- Rayleigh-Ritz on the unlocked columns ---
+    phase_begin();
+    T* Q2 = V + (size_t)k * n;
+    rc = gemm<T>(st, false, n, nu, n, A, lda, Q2, n, AQ, n, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
+                 scr, false, false, &h->launches);
+    if (!rc) rc = gemm<T>(st, true, nu, nu, n, Q2, n, AQ, n, H, nu, 1.0, 0.0, nullptr, 0, 0.0,
+                          nullptr, 0, scr, true, false, &h->launches);
+    if (!rc) rc = herm_fill_lower<T>(st, nu, H, nu, &h->launches);
+    int sweeps = 0;
+    if (!rc) rc = jacobi_eig<T>(st, nu, H, nu, Wm, nu, dw, jac, jac_bytes, 40, &sweeps, &h->launches);
+    // V <- Q2 W (via T2), AV = AQ W (into P)
+    if (!rc) rc = gemm<T>(st, false, n, nu, nu, Q2, n, Wm, nu, T2, n, 1.0, 0.0, nullptr, 0, 0.0,
+                          nullptr, 0, scr, false, false, &h->launches);
+    if (!rc) rc = gemm<T>(st, false, n, nu, nu, AQ, n, Wm, nu, P, n, 1.0, 0.0, nullptr, 0, 0.0,
+                          nullptr, 0, scr, false, false, &h->launches);
+    if (!rc) rc = copy_cols<T>(st, n, nu, T2, n, Q2, n, &h->launches);
+    phase_end(S.t_rr);
+    if (rc) break;
+    // --- residuals (eq. res) ---
+    phase_begin();
+    rc = resid_norms<T>(st, n, nu, P, n, Q2, n, dw, dres, &h->launches);
+    if (!rc) rc = (cudaMemcpyAsync(hw, dw, sizeof(double) * nu, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                   cudaMemcpyAsync(hr, dres, sizeof(double) * nu, cudaMemcpyDeviceToHost, st) == cudaSuccess)
+                      ? 0 : CHASE_ERR_CUDA;
+    phase_end(S.t_resid);
+    if (rc) break;
+    for (int a = 0; a < nu; ++a) {
+      ritz[k + a] = hw[a];
+      res[k + a] = hr[a];
+    }
+    // --- locking: contiguous converged prefix among the first nev ---
+    int knew = k;
+    while (knew < nev && res[knew] < cfg.tol) ++knew;
+    if (logs && it < log_cap) {
+      chase_iter_log& g = logs[it];
+      g.iteration = it + 1; g.locked_before = k; g.locked_after = knew; g.variant = variant;
+      g.chol_fail_info = fi; g.deg_min = deg[k]; g.deg_max = deg[l - 1]; g.matvecs = matvecs;
+      g.log_cond_est = lest; g.c = c; g.e = e; g.mu1 = mu1; g.mu_ell = mu_ell;
+    }
+    for (int a = k; a < l; ++a) mu1 = std::min(mu1, ritz[a]);
+    mu_ell = ritz[l - 1];
+    for (int a = k; a < l; ++a) mu_ell = std::max(mu_ell, ritz[a]);
+    k = knew;
+    if (k >= nev) {
+      status = CHASE_OK;
+      ++it;
+      break;
+    }
+    // --- degrees of the unlocked columns, ascending order ---
+    if (cfg.opt_degree) {
+      const double c2 = 0.5 * (bsup + mu_ell), e2 = 0.5 * (bsup - mu_ell);
+      for (int a = k; a < l; ++a) {
+        const double lr = std::log(abs_rho(ritz[a], c2, e2));
+        int m;
+        if (lr <= 0.0) m = cfg.deg_max;
+        else if (!(res[a] > cfg.tol)) m = cfg.deg_min;
+        else {
+          const double mm = std::ceil(std::log(res[a] / cfg.tol) / lr);
+          m = (mm > cfg.deg_max) ? cfg.deg_max : (int)mm;
+        }
+        m = std::max(cfg.deg_min, std::min(cfg.deg_max, m));
+        deg[a] = m;
+      }
+      // stable sort of [k, l) by degree; apply the permutation to V's columns
+      std::vector<int> idx(l - k);
+      std::iota(idx.begin(), idx.end(), k);
+      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return deg[x] < deg[y]; });
+      bool moved = false;
+      for (int a = 0; a < l - k; ++a) moved |= (idx[a] != k + a);
+      if (moved) {
+        std::vector<int> d2(l - k), dd(l - k);
+        std::vector<double> r2(l - k), s2(l - k);
+        int* hperm = (int*)(h->hbuf + 2 * (size_t)l);
+        for (int a = 0; a < l - k; ++a) {
+          d2[a] = deg[idx[a]]; r2[a] = ritz[idx[a]]; s2[a] = res[idx[a]];
+          hperm[a] = idx[a] - k;
+        }
+        for (int a = 0; a < l - k; ++a) { deg[k + a] = d2[a]; ritz[k + a] = r2[a]; res[k + a] = s2[a]; }
+        int* dperm = (int*)jac;  // Jacobi workspace is free here
+        CHASE_CUDA_TRY(cudaMemcpyAsync(dperm, hperm, sizeof(int) * (l - k), cudaMemcpyHostToDevice, st));
+        TRY(copy_cols<T>(st, n, l - k, V + (size_t)k * n, n, T2, n, &h->launches));
+        TRY(gather_cols<T>(st, n, l - k, T2, n, dperm, V + (size_t)k * n, n, &h->launches));
+        CHASE_CUDA_TRY(cudaStreamSynchronize(st));  // hperm lives in the staging buffer
+      }
+    } else {
+      for (int a = k; a < l; ++a) deg[a] = cfg.deg_init;
+    }
+  }
+  if (rc) {
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(t0); cudaEventDestroy(t1);
+    return rc;
+  }
+  // locked pairs ascending (selection order over the locked prefix)
+  const int kout = std::min(k, nev);
+  std::vector<int> ord(l);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.begin() + kout, [&](int x, int y) { return ritz[x] < ritz[y]; });
+  bool moved = false;
+  for (int a = 0; a < kout; ++a) moved |= (ord[a] != a);
+  if (moved) {
+    int* hperm = (int*)(h->hbuf + 2 * (size_t)l);
+    for (int a = 0; a < l; ++a) hperm[a] = ord[a];
+    int* dperm = (int*)jac;
+    CHASE_CUDA_TRY(cudaMemcpyAsync(dperm, hperm, sizeof(int) * l, cudaMemcpyHostToDevice, st));
+    TRY(copy_cols<T>(st, n, l, V, n, T2, n, &h->launches));
+    TRY(gather_cols<T>(st, n, l, T2, n, dperm, V, n, &h->launches));
+  }
+  TRY(copy_cols<T>(st, n, l, V, n, dV, ldv, &h->launches));
+  cudaEventRecord(t1, st);
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  S.t_total = elapsed_s(t0, t1);
+  for (int a = 0; a < nev; ++a) {
+    evals[a] = ritz[ord[a]];
+    resid[a] = res[ord[a]];
+  }
+  S.iterations = it;
+  S.locked = k;
+  S.matvecs = matvecs;
+  if (stats) *stats = S;
+  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(t0); cudaEventDestroy(t1);
+  return status;
+}
+
+template <class T>
+int filter_impl(chase_ctx* h, int n, const T* A, int lda, int ncols, const T* dV, int ldv,
+                const int* degrees, double c, double e, double lambda1, T* dVout, int ldo) {
+  cudaStream_t st = h->stream;
+  const size_t blk = align256(sizeof(T) * (size_t)n * ncols);
+  TRY(ensure_ws(h, blk + kScratchBytes));
+  T* P = (T*)h->ws;
+  Scratch scr{(char*)h->ws + blk, kScratchBytes};
+  if (dVout != dV) TRY(copy_cols<T>(st, n, ncols, dV, ldv, dVout, ldo, &h->launches));
+  double fl = 0.0;
+  TRY(filter_inplace<T>(h, n, A, lda, ncols, dVout, ldo, P, n, degrees, c, e, lambda1, scr, &fl));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  return 0;
+}
+
+template <class T>
+int qr_impl(chase_ctx* h, int n, int l, T* X, int ldx, double est, int force, int* variant_used,
+            int* chol_info) {
+  cudaStream_t st = h->stream;
+  const size_t blk = align256(sizeof(T) * (size_t)n * l);
+  const size_t sq = align256(sizeof(T) * (size_t)l * l);
+  TRY(ensure_ws(h, 2 * blk + 2 * sq + kScratchBytes));
+  char* base = (char*)h->ws;
+  T* Xtmp = (T*)base;
+  T* Xsave = (T*)(base + blk);
+  T* G = (T*)(base + 2 * blk);
+  T* Ri = (T*)(base + 2 * blk + sq);
+  Scratch scr{base + 2 * blk + 2 * sq, kScratchBytes};
+  double lest = (est > 0.0) ? std::log(est) : -1e300;
+  if (!std::isfinite(est) && est > 0) lest = 1e300;
+  int v = 0, fi = 0;
+  int rc = qr_dynamic<T>(h, n, l, X, ldx, lest, 1e8, 20.0, force, Xtmp, Xsave, G, Ri, scr, &v, &fi);
+  if (variant_used) *variant_used = v;
+  if (chol_info) *chol_info = fi;
+  if (rc && rc != CHASE_CHOL_FAILED) return rc;
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  return rc;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+int chase_config_default(chase_config* cfg) {
+  if (!cfg) return -1;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->tol = 1e-10;
+  cfg->max_iter = 25;
+  cfg->deg_init = 20;
+  cfg->deg_min = 10;
+  cfg->deg_max = 36;
+  cfg->opt_degree = 1;
+  cfg->eta = 1.0;
+  cfg->cond_hi = 1e8;
+  cfg->cond_lo = 20.0;
+  cfg->qr_force = CHASE_QR_AUTO;
+  cfg->prec = CHASE_FP64;
+  return CHASE_OK;
+}
+
+int chase_create(chase_handle* hp, int device, void* cuda_stream) {
+  if (!hp) return -1;
+  *hp = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return device < 0 ? -2 : CHASE_ERR_CUDA;
+  }
+  chase_ctx* h = new chase_ctx();
+  h->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete h; return CHASE_ERR_CUDA; }
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) { delete h; return CHASE_ERR_CUDA; }
+    h->own_stream = true;
+  }
+  if (cudaMalloc((void**)&h->dstat, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->hstat, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    chase_destroy(h);
+    return CHASE_ERR_OOM;
+  }
+  *hp = h;
+  return CHASE_OK;
+}
+
+int chase_destroy(chase_handle h) {
+  if (!h) return -1;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->ws) cudaFree(h->ws);
+  if (h->dstat) cudaFree(h->dstat);
+  if (h->hstat) cudaFreeHost(h->hstat);
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return CHASE_OK;
+}
+
+int chase_workspace_bytes(chase_dtype dtype, int n, int nev, int nex, chase_precision prec,
+                          size_t* bytes) {
+  if (dtype != CHASE_R64 && dtype != CHASE_C128) return -1;
+  if (n < 1) return -2;
+  if (nev < 1) return -3;
+  if (nex < 0 || nev + nex > n) return -4;
+  (void)prec;
+  if (!bytes) return -6;
+  *bytes = (dtype == CHASE_R64) ? layout_for<double>(n, nev + nex).total
+                                : layout_for<z64>(n, nev + nex).total;
+  return CHASE_OK;
+}
+
+int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda, int nev, int nex,
+                const chase_config* cfg, const chase_bounds* bounds, void* dV, int ldv,
+                double* evals, double* resid, chase_stats* stats, chase_iter_log* log,
+                int log_cap) {
+  if (!h) return -1;
+  if (dtype != CHASE_R64 && dtype != CHASE_C128) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < n) return -5;
+  if (nev < 1) return -6;
+  if (nex < 0 || nev + nex > n) return -7;
+  chase_config c;
+  if (cfg) c = *cfg; else chase_config_default(&c);
+  if (!(c.tol > 0.0) || c.max_iter < 0 || c.deg_init < 1 || c.deg_min < 1 || c.deg_max < c.deg_min ||
+      !(c.eta > 0.0) || c.qr_force < 0 || c.qr_force > 4)
+    return -8;
+  if (c.prec != CHASE_FP64) return CHASE_ERR_UNSUPPORTED;
+  if (!bounds || !(bounds->b_sup > bounds->lambda_ell) || !(bounds->lambda_ell >= bounds->lambda1))
+    return -9;
+  if (!dV) return -10;
+  if (ldv < n) return -11;
+  if (!evals) return -12;
+  if (!resid) return -13;
+  if (log_cap < 0) return -16;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  if (dtype == CHASE_R64)
+    return solve_impl<double>(h, n, (const double*)dA, lda, nev, nex, c, *bounds, (double*)dV, ldv,
+                              evals, resid, stats, log, log_cap);
+  return solve_impl<z64>(h, n, (const z64*)dA, lda, nev, nex, c, *bounds, (z64*)dV, ldv, evals,
+                         resid, stats, log, log_cap);
+}
+
+int chase_filter(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda, int ncols,
+                 const void* dV, int ldv, const int* degrees, double c, double e, double lambda1,
+                 chase_precision prec, void* dVout, int ldvout) {
+  if (!h) return -1;
+  if (dtype != CHASE_R64 && dtype != CHASE_C128) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < n) return -5;
+  if (ncols < 0) return -6;
+  if (ncols > 0 && !dV) return -7;
+  if (ldv < n) return -8;
+  if (ncols > 0 && !degrees) return -9;
+  for (int a = 0; a < ncols; ++a)
+    if (degrees[a] < 0 || (a > 0 && degrees[a] < degrees[a - 1])) return -9;
+  if (!(e > 0.0) || !std::isfinite(c)) return -11;
+  if (!(lambda1 < c - e)) return -12;
+  if (prec != CHASE_FP64) return CHASE_ERR_UNSUPPORTED;
+  if (ncols > 0 && !dVout) return -14;
+  if (ldvout < n) return -15;
+  if (ncols == 0) return CHASE_OK;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  if (dtype == CHASE_R64)
+    return filter_impl<double>(h, n, (const double*)dA, lda, ncols, (const double*)dV, ldv, degrees,
+                               c, e, lambda1, (double*)dVout, ldvout);
+  return filter_impl<z64>(h, n, (const z64*)dA, lda, ncols, (const z64*)dV, ldv, degrees, c, e,
+                          lambda1, (z64*)dVout, ldvout);
+}
+
+int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int ldx,
+             double est_cond, int qr_force, int* variant_used, int* chol_info) {
+  if (!h) return -1;
+  if (dtype != CHASE_R64 && dtype != CHASE_C128) return -2;
+  if (n < 1) return -3;
+  if (ncols < 1 || ncols > n) return -4;
+  if (!dX) return -5;
+  if (ldx < n) return -6;
+  if (std::isnan(est_cond)) return -7;
+  if (qr_force < 0 || qr_force > 4) return -8;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  if (dtype == CHASE_R64)
+    return qr_impl<double>(h, n, ncols, (double*)dX, ldx, est_cond, qr_force, variant_used, chol_info);
+  return qr_impl<z64>(h, n, ncols, (z64*)dX, ldx, est_cond, qr_force, variant_used, chol_info);
+}
+
+int chase_cond_est(int ell, int nlocked, const double* ritz, const int* degrees, double lambda1,
+                   double c, double e, double eta, double* est, double* log_est) {
+  if (ell < 1) return -1;
+  if (nlocked < 0 || nlocked >= ell) return -2;
+  if (!ritz) return -3;
+  if (!degrees) return -4;
+  if (!(e > 0.0)) return -7;
+  if (!(eta > 0.0)) return -8;
+  if (!est) return -9;
+  const double l = log_cond_est(ritz[nlocked], degrees[nlocked], degrees[ell - 1], lambda1, c, e, eta);
+  *est = std::exp(l);
+  if (log_est) *log_est = l;
+  return CHASE_OK;
+}
+
+const char* chase_status_string(int status) {
+  if (status < 0) return "invalid argument";
+  switch (status) {
+    case CHASE_OK: return "ok";
+    case CHASE_NOT_CONVERGED: return "not converged within max_iter";
+    case CHASE_CHOL_FAILED: return "Cholesky factorisation failed";
+    case CHASE_ERR_CUDA: return "CUDA error";
+    case CHASE_ERR_OOM: return "out of device memory";
+    case CHASE_ERR_TIMEOUT: return "device wait timed out";
+    case CHASE_ERR_NONFINITE: return "non-finite value in the input";
+    case CHASE_ERR_UNSUPPORTED: return "option not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"
