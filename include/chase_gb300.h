@@ -90,7 +90,9 @@ typedef struct {
   int n_chol1, n_chol2, n_shifted, n_hhqr; /* QR variant used per iteration */
   int n_chol_failures;     /* Cholesky failures that triggered an escalation */
   double t_total, t_filter, t_qr, t_rr, t_resid; /* seconds, CUDA-event timed */
-  double filter_flops;     /* algorithmic flops of the filter products */
+  double filter_flops;     /* algorithmic flops of the filter products (2n^2 / 8n^2 per MatVec) */
+  int kernel_launches;     /* CUDA kernels this call launched */
+  int filter_launches;     /* of which filter product launches (one per filter step) */
 } chase_stats;
 
 /* Per-iteration record (the kind of data Figure 2 plots). */

@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("n_chol1", ctypes.c_int), ("n_chol2", ctypes.c_int), ("n_shifted", ctypes.c_int),
                 ("n_hhqr", ctypes.c_int), ("n_chol_failures", ctypes.c_int),
                 ("t_total", ctypes.c_double), ("t_filter", ctypes.c_double), ("t_qr", ctypes.c_double),
-                ("t_rr", ctypes.c_double), ("t_resid", ctypes.c_double), ("filter_flops", ctypes.c_double)]
+                ("t_rr", ctypes.c_double), ("t_resid", ctypes.c_double), ("filter_flops", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int), ("filter_launches", ctypes.c_int)]
 
 
 class IterLog(ctypes.Structure):

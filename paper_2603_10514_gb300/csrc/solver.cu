@@ -129,7 +129,7 @@ double elapsed_s(cudaEvent_t a, cudaEvent_t b) {
 template <class T>
 int filter_inplace(chase_ctx* h, int n, const T* A, int lda, int ncols, T* V, int ldv, T* P,
                    int ldp, const int* deg, double c, double e, double lambda1, Scratch scr,
-                   double* flops) {
+                   double* flops, int* steps = nullptr) {
   cudaStream_t st = h->stream;
   if (ncols <= 0) return 0;
   const int mmax = deg[ncols - 1];
@@ -160,6 +160,7 @@ int filter_inplace(chase_ctx* h, int n, const T* A, int lda, int ncols, T* V, in
                 out + (size_t)first * ldo, ldo, alpha, beta, in + (size_t)first * ldi, ldi, gamma,
                 out + (size_t)first * ldo, ldo, scr, false, false, &h->launches));
     if (flops) *flops += per_col * act;
+    if (steps) ++*steps;
   }
   // copy back the columns whose final result sits in P (odd degree)
   int a = 0;
@@ -298,6 +299,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
   cudaEventRecord(t0, st);
 
   int rc = 0;
+  const int launches0 = h->launches;
   std::vector<int> deg(l, cfg.deg_init);
   std::vector<double> ritz(l, bd.lambda1), res(l, 1.0);
   std::vector<int> perm(l);
@@ -329,7 +331,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     // --- filter ---
     phase_begin();
     rc = filter_inplace<T>(h, n, A, lda, nu, V + (size_t)k * n, n, P, n, deg.data() + k, c, e, mu1,
-                           scr, &S.filter_flops);
+                           scr, &S.filter_flops, &S.filter_launches);
     phase_end(S.t_filter);
     if (rc) break;
     for (int a = k; a < l; ++a) matvecs += deg[a];
@@ -467,6 +469,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
   S.iterations = it;
   S.locked = k;
   S.matvecs = matvecs;
+  S.kernel_launches = h->launches - launches0;
   if (stats) *stats = S;
   cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(t0); cudaEventDestroy(t1);
   return status;
