@@ -54,7 +54,8 @@ typedef enum {
   CHASE_ERR_OOM = 4,        /* workspace allocation failed */
   CHASE_ERR_TIMEOUT = 5,    /* a bounded device wait gave up */
   CHASE_ERR_NONFINITE = 6,  /* NaN/Inf met in the data */
-  CHASE_ERR_UNSUPPORTED = 7 /* option not available in this build */
+  CHASE_ERR_UNSUPPORTED = 7, /* option not available in this build */
+  CHASE_ERR_TOO_LARGE = 8    /* problem exceeds chase_filter_noalloc's fixed scratch */
 } chase_status;
 
 /* Variant codes of Algorithm 3 (also used by qr_force). */
@@ -182,6 +183,42 @@ int chase_cond_est(int ell, int nlocked, const double* ritz, const int* degrees,
 
 /* Static description of a status code. */
 const char* chase_status_string(int status);
+
+/* Size of the fixed device scratch array behind chase_filter_noalloc (32 MiB). */
+#define CHASE_FILTER_NOALLOC_MAX_BYTES ((size_t)32 << 20)
+
+/*
+ * chase_filter_noalloc -- the same filter as chase_filter, for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this is a
+ * deployment variant of the library's filter, not a step of the method.
+ *
+ * chase_filter (like every handle-based call) grows a device workspace with
+ * cudaMalloc on demand.  Some callers cannot let a library do that: code that
+ * runs while a CUDA graph is being captured (cudaMalloc cannot be recorded),
+ * serving processes that reserve all of HBM in their own pool up front, and
+ * latency-critical loops where cudaMalloc / cudaFree would synchronise the
+ * device.  This entry point calls no allocating routine: its scratch (the
+ * recurrence's second n x ncols buffer and the split-K partial sums) lives in
+ * one file-scope device array of CHASE_FILTER_NOALLOC_MAX_BYTES that every GPU
+ * loading the library holds until the process exits.
+ *
+ * Arguments as chase_filter (FP64 only), without a handle: the work is ordered
+ * on `cuda_stream` (a cudaStream_t, NULL = legacy default stream) of the
+ * current device, and the call returns after it completes.  The caller passes
+ * and owns dV and dVout as before.
+ * Limits and behaviour:
+ *   - sizeof(element) * n * ncols must be <= CHASE_FILTER_NOALLOC_MAX_BYTES,
+ *     otherwise CHASE_ERR_TOO_LARGE is returned and nothing is done.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the array, which keeps the last call's
+ *     contents (nothing in it needs to start at zero).  Calls that overlap on
+ *     the GPU race on it: order them on one stream.
+ */
+int chase_filter_noalloc(chase_dtype dtype, int n, const void* dA, int lda, int ncols,
+                         const void* dV, int ldv, const int* degrees, double c, double e,
+                         double lambda1, void* dVout, int ldvout, void* cuda_stream);
 
 #ifdef __cplusplus
 }

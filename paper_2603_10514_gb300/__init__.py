@@ -23,10 +23,13 @@ CHASE_R64, CHASE_C128 = 0, 1
 CHASE_FP64, CHASE_TF32, CHASE_BF16X3 = 0, 1, 2
 CHASE_OK, CHASE_NOT_CONVERGED, CHASE_CHOL_FAILED = 0, 1, 2
 CHASE_ERR_CUDA, CHASE_ERR_OOM, CHASE_ERR_TIMEOUT, CHASE_ERR_NONFINITE, CHASE_ERR_UNSUPPORTED = 3, 4, 5, 6, 7
+CHASE_ERR_TOO_LARGE = 8
+CHASE_FILTER_NOALLOC_MAX_BYTES = 32 << 20
 QR_VARIANTS = {1: "cholqr1", 2: "cholqr2", 3: "shifted_cholqr2", 4: "householder"}
 
 EXPORTED = ["chase_create", "chase_destroy", "chase_config_default", "chase_workspace_bytes",
-            "chase_solve", "chase_filter", "chase_qr", "chase_cond_est", "chase_status_string"]
+            "chase_solve", "chase_filter", "chase_qr", "chase_cond_est", "chase_status_string",
+            "chase_filter_noalloc"]
 
 
 class ChaseError(RuntimeError):
@@ -91,6 +94,7 @@ def lib():
         L.chase_filter.argtypes = [P, i, i, P, i, i, P, i, P, d, d, d, i, P, i]
         L.chase_qr.argtypes = [P, i, i, i, P, i, d, i, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.chase_cond_est.argtypes = [i, i, P, P, d, d, d, d, ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.chase_filter_noalloc.argtypes = [i, i, P, i, i, P, i, P, d, d, d, P, i, P]
         L.chase_status_string.argtypes = [i]
         L.chase_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -236,3 +240,31 @@ def chase_cond_est(ritz, degrees, nlocked, lambda1, c, e, eta=1.0):
     if rc:
         raise ChaseError(rc, "chase_cond_est")
     return est.value, lest.value
+
+
+def chase_filter_noalloc(A, V, degrees, c, e, lambda1, out=None, stream=None):
+    """The filter of chase_filter for callers that cannot allocate device memory (inside
+    a CUDA graph capture, under a pre-reserved memory pool, or in latency-critical loops
+    where cudaMalloc would synchronise the device).  Its scratch is a fixed 32 MiB device
+    array inside the library; `out` (if given) and V are the caller's buffers.  Work is
+    ordered on `stream` (default: torch's current stream of V's device).  Raises
+    ChaseError(CHASE_ERR_TOO_LARGE) when n * ncols elements exceed the fixed scratch."""
+    import torch
+    n, ncols = V.shape
+    dt = _dtype_code(A)
+    lda, ldv = _ld(A, "A"), _ld(V, "V")
+    if out is None:
+        out = colmajor(torch.empty_like(V))
+    ldo = _ld(out, "out")
+    deg = np.ascontiguousarray(degrees, dtype=np.int32)
+    if stream is None:
+        stream = torch.cuda.current_stream(V.device).cuda_stream
+    with torch.cuda.device(V.device):
+        rc = lib().chase_filter_noalloc(dt, n, ctypes.c_void_p(A.data_ptr()), lda, ncols,
+                                        ctypes.c_void_p(V.data_ptr()), ldv,
+                                        deg.ctypes.data_as(ctypes.c_void_p), float(c), float(e),
+                                        float(lambda1), ctypes.c_void_p(out.data_ptr()), ldo,
+                                        ctypes.c_void_p(stream))
+    if rc:
+        raise ChaseError(rc, "chase_filter_noalloc")
+    return out

@@ -693,6 +693,7 @@ const char* chase_status_string(int status) {
     case CHASE_ERR_TIMEOUT: return "device wait timed out";
     case CHASE_ERR_NONFINITE: return "non-finite value in the input";
     case CHASE_ERR_UNSUPPORTED: return "option not supported by this build";
+    case CHASE_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of chase_filter_noalloc";
     default: return "unknown status";
   }
 }
