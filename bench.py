@@ -36,8 +36,9 @@ METRIC = ("time-to-solution for nev pairs at resid<=1e-10 & filter TFLOP/s vs FP
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
-# iteration); used to scale the oracle's timed sample to a whole solve.
-REF_MATVECS_PER_SOLVE = None
+# iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
+# GB300: 114037 filter MatVecs + 8690 Rayleigh-Ritz / residual products over 9 iterations.
+REF_MATVECS_PER_SOLVE = 122727
 
 
 def parse():
@@ -52,7 +53,48 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=8)
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter"],
+                    help="solve: the headline time-to-solution; filter: chase_filter alone "
+                         "(kernel-level timing and small cases for profilers)")
+    ap.add_argument("--ncols", type=int, default=600, help="filter mode: block width")
+    ap.add_argument("--degree", type=int, default=20, help="filter mode: degree of every column")
     return ap.parse_args()
+
+
+def run_filter(args):
+    """chase_filter on n x ncols, every column at the same degree: filter TFLOP/s from CUDA
+    events on the handle's stream (FP64 complex, 8 n^2 flops per column MatVec)."""
+    import numpy as np
+    import torch
+
+    import paper_2603_10514_gb300 as P
+    import workloads as W
+    P.build()
+    n, k = args.n, args.ncols
+    lam = W.spectrum_clustered(n, min(k, n), 2)
+    A = W.known_spectrum_matrix(lam, 2, True, device="cuda")
+    V = torch.from_numpy(np.ascontiguousarray(W.start_block(n, k, 2, True).T)).cuda().mT
+    out = torch.empty_like(V.mT).mT
+    l1, le, bs = W.bounds_for(lam, k)
+    c, e = 0.5 * (bs + le), 0.5 * (bs - le)
+    stream = torch.cuda.current_stream()
+    h = P.Handle(0, stream=stream.cuda_stream)
+    degs = [args.degree] * k
+    for _ in range(args.warmup):
+        P.chase_filter(h, A, V, degs, c, e, l1, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        P.chase_filter(h, A, V, degs, c, e, l1, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    flops = 8.0 * n * n * k * args.degree
+    h.close()
+    print(json.dumps({"mode": "filter", "n": n, "ncols": k, "degree": args.degree,
+                      "s_per_filter": t, "tflops": flops / t / 1e12,
+                      "frac_of_fp64_peak": flops / t / 1e12 / FP64_PEAK_TFLOPS}), flush=True)
 
 
 class ClockSampler:
@@ -186,6 +228,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.mode == "filter":
+        run_filter(args)
         return
     import numpy as np
     import torch

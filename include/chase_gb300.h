@@ -73,8 +73,11 @@ typedef struct {
   double cond_hi;    /* Algorithm 3: shifted CholeskyQR2 above this estimate (1e8) */
   double cond_lo;    /* Algorithm 3: CholeskyQR1 below this estimate (20) */
   int qr_force;      /* CHASE_QR_AUTO or a forced variant */
-  chase_precision prec; /* filter arithmetic */
-  int reserved[8];
+  chase_precision prec; /* filter arithmetic: CHASE_FP64, or CHASE_BF16X3 for the mixed mode */
+  double mp_switch;  /* mixed mode: the filter runs in BF16x3 until the largest residual of the
+                        unlocked wanted pairs drops to mp_switch * max(|lambda1|, |b_sup|),
+                        then in FP64 for the remaining iterations (default 1e-3) */
+  int reserved[6];
 } chase_config;
 
 /* Spectral information the filter needs (Algorithm 1, step "estimate lambda_1,
@@ -94,6 +97,9 @@ typedef struct {
   double filter_flops;     /* algorithmic flops of the filter products (2n^2 / 8n^2 per MatVec) */
   int kernel_launches;     /* CUDA kernels this call launched */
   int filter_launches;     /* of which filter product launches (one per filter step) */
+  int n_lowprec_iters;     /* iterations whose filter ran in BF16x3 */
+  double t_filter_lowprec; /* seconds of those filters */
+  double filter_flops_lowprec; /* their algorithmic flops (counted as for FP64) */
 } chase_stats;
 
 /* Per-iteration record (the kind of data Figure 2 plots). */
@@ -117,6 +123,10 @@ int chase_config_default(chase_config* cfg);
 /* Device workspace chase_solve needs for this problem shape (bytes). */
 int chase_workspace_bytes(chase_dtype dtype, int n, int nev, int nex, chase_precision prec,
                           size_t* bytes);
+
+/* Grows the handle's workspace to at least `bytes` now, so that later calls of
+ * that size allocate nothing (a service sizes its handles once at start-up). */
+int chase_reserve_workspace(chase_handle h, size_t bytes);
 
 /*
  * chase_solve -- Algorithm 1.
@@ -147,7 +157,9 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
  *   degrees   host, ncols ints, ascending, each >= 0 (0 copies the column).
  *   dV        device n x ncols input (not modified); dVout device n x ncols
  *             output (may equal dV).
- *   prec      CHASE_FP64 (others: CHASE_ERR_UNSUPPORTED when not built).
+ *   prec      CHASE_FP64, or CHASE_BF16X3: each A*V product as three BF16
+ *             tensor-core products (hi/lo splits, FP32 accumulation), the
+ *             recurrence itself in FP64 (CHASE_TF32: CHASE_ERR_UNSUPPORTED).
  */
 int chase_filter(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda, int ncols,
                  const void* dV, int ldv, const int* degrees, double c, double e, double lambda1,

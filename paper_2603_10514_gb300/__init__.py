@@ -29,7 +29,7 @@ QR_VARIANTS = {1: "cholqr1", 2: "cholqr2", 3: "shifted_cholqr2", 4: "householder
 
 EXPORTED = ["chase_create", "chase_destroy", "chase_config_default", "chase_workspace_bytes",
             "chase_solve", "chase_filter", "chase_qr", "chase_cond_est", "chase_status_string",
-            "chase_filter_noalloc"]
+            "chase_filter_noalloc", "chase_reserve_workspace"]
 
 
 class ChaseError(RuntimeError):
@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("deg_init", ctypes.c_int),
                 ("deg_min", ctypes.c_int), ("deg_max", ctypes.c_int), ("opt_degree", ctypes.c_int),
                 ("eta", ctypes.c_double), ("cond_hi", ctypes.c_double), ("cond_lo", ctypes.c_double),
-                ("qr_force", ctypes.c_int), ("prec", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("qr_force", ctypes.c_int), ("prec", ctypes.c_int), ("mp_switch", ctypes.c_double),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class Bounds(ctypes.Structure):
@@ -55,7 +56,9 @@ class Stats(ctypes.Structure):
                 ("n_hhqr", ctypes.c_int), ("n_chol_failures", ctypes.c_int),
                 ("t_total", ctypes.c_double), ("t_filter", ctypes.c_double), ("t_qr", ctypes.c_double),
                 ("t_rr", ctypes.c_double), ("t_resid", ctypes.c_double), ("filter_flops", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int), ("filter_launches", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("filter_launches", ctypes.c_int),
+                ("n_lowprec_iters", ctypes.c_int), ("t_filter_lowprec", ctypes.c_double),
+                ("filter_flops_lowprec", ctypes.c_double)]
 
 
 class IterLog(ctypes.Structure):
@@ -89,6 +92,7 @@ def lib():
         L.chase_destroy.argtypes = [P]
         L.chase_config_default.argtypes = [ctypes.POINTER(Config)]
         L.chase_workspace_bytes.argtypes = [i, i, i, i, i, ctypes.POINTER(ctypes.c_size_t)]
+        L.chase_reserve_workspace.argtypes = [P, ctypes.c_size_t]
         L.chase_solve.argtypes = [P, i, i, P, i, i, i, ctypes.POINTER(Config), ctypes.POINTER(Bounds),
                                   P, i, P, P, ctypes.POINTER(Stats), P, i]
         L.chase_filter.argtypes = [P, i, i, P, i, i, P, i, P, d, d, d, i, P, i]
@@ -168,6 +172,12 @@ class Handle:
     @property
     def ptr(self):
         return self._h
+
+    def reserve(self, nbytes):
+        """Grow the workspace to nbytes now (no allocation later for problems that fit)."""
+        rc = lib().chase_reserve_workspace(self._h, int(nbytes))
+        if rc:
+            raise ChaseError(rc, "chase_reserve_workspace")
 
 
 def chase_solve(h, A, V, nev, nex, bounds, cfg=None, log_cap=64, check=True):

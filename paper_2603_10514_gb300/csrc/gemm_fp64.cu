@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(int M, int N, int K, const T* 
   __shared__ T Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // column tiles vary fastest so that the CTAs in flight share A's row panels in L2
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
   if (upper_only && m0 > n0 + BN - 1) return;
   const int kb = blockIdx.z * kchunk;
   int ke = min(K, kb + kchunk);
@@ -194,7 +195,7 @@ int gemm(cudaStream_t st, bool transA, int M, int N, int K, const T* A, int lda,
   }
   if (K <= 0) { S = 1; kchunk = 0; }
   T* partial = (S > 1) ? (T*)scratch.ptr : nullptr;
-  dim3 grid(tm, tn, S);
+  dim3 grid(tn, tm, S);
   if (transA) {
     if (TN == 2) launch_gemm<T, true, 2>(st, grid, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, X, ldx, gamma, Y, ldy, kchunk, partial, upper_only, tri_b);
     else         launch_gemm<T, true, 1>(st, grid, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, X, ldx, gamma, Y, ldy, kchunk, partial, upper_only, tri_b);

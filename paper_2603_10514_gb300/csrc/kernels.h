@@ -65,4 +65,23 @@ template <class T>
 int nonfinite_check(cudaStream_t st, int n, int ncols, const T* X, int ldx, DevStatus* dst,
                     int* launches);
 
+// ---- tensor-core (tcgen05) split-BF16 filter product (gemm_tc.cu) ---------
+// Stacked-real operands: M = n (real) or 2n (complex) rows; kp = M rounded up to 64.
+int tc_kpad(int M);
+template <class T>
+int tc_split_A(cudaStream_t st, int n, const T* A, int lda, int kp, void* Ah, void* Al,
+               int* launches);
+template <class T>
+int tc_split_V(cudaStream_t st, int n, int ncols, const T* V, int ldv, double* V64, int ldo, int kp,
+               void* Vh, void* Vl, int* launches);
+template <class T>
+int tc_unstack_V(cudaStream_t st, int n, int c0, int c1, const double* V64, int ldi, T* V, int ldv,
+                 int* launches);
+// One filter step on columns [col0, col0 + N) of the stacked block (ld kp everywhere).
+int tc_filter_step(cudaStream_t st, int M, int kp, const void* Ah, const void* Al,
+                   const void* Vh_in, const void* Vl_in, int ncols_total, int col0, int N,
+                   double alpha, double beta, const double* X64, double gamma, const double* Z64,
+                   double* out64, int ldv, void* Vh_out, void* Vl_out, DevStatus* dst,
+                   int* launches);
+
 }  // namespace chase

@@ -174,6 +174,99 @@ int filter_inplace(chase_ctx* h, int n, const T* A, int lda, int ncols, T* V, in
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision (BF16x3 on tcgen05) Algorithm 4.  The block is kept in FP64
+// ("stacked real": [Re; Im] for complex) in two ping-pong buffers, and its BF16
+// hi/lo split in two more; A's split planes are prepared once per call site.
+// ---------------------------------------------------------------------------
+struct TcBufs {
+  int M = 0, kp = 0, ncols = 0;
+  void* Ah = nullptr;
+  void* Al = nullptr;
+  double* V64[2] = {nullptr, nullptr};
+  void* Vh[2] = {nullptr, nullptr};
+  void* Vl[2] = {nullptr, nullptr};
+};
+
+template <class T>
+size_t tc_bytes(int n, int ncols) {
+  const int M = Sc<T>::cplx ? 2 * n : n;
+  const size_t kp = (size_t)tc_kpad(M);
+  return 2 * align256(2 * (size_t)M * kp) + 2 * align256(8 * kp * ncols) +
+         4 * align256(2 * kp * ncols);
+}
+
+template <class T>
+TcBufs tc_carve(char* base, int n, int ncols) {
+  TcBufs B;
+  B.M = Sc<T>::cplx ? 2 * n : n;
+  B.kp = tc_kpad(B.M);
+  B.ncols = ncols;
+  size_t off = 0;
+  const size_t ab = align256(2 * (size_t)B.M * B.kp);
+  const size_t vb64 = align256(8 * (size_t)B.kp * ncols);
+  const size_t vb16 = align256(2 * (size_t)B.kp * ncols);
+  B.Ah = base + off; off += ab;
+  B.Al = base + off; off += ab;
+  for (int i = 0; i < 2; ++i) { B.V64[i] = (double*)(base + off); off += vb64; }
+  for (int i = 0; i < 2; ++i) { B.Vh[i] = base + off; off += vb16; B.Vl[i] = base + off; off += vb16; }
+  return B;
+}
+
+template <class T>
+int filter_mixed(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols, T* V, int ldv,
+                 const int* deg, double c, double e, double lambda1, TcBufs& B, double* flops,
+                 int* steps) {
+  cudaStream_t st = h->stream;
+  if (ncols <= 0) return 0;
+  const int M = B.M, kp = B.kp;
+  if (split_A) TRY(tc_split_A<T>(st, n, A, lda, kp, B.Ah, B.Al, &h->launches));
+  TRY(tc_split_V<T>(st, n, ncols, V, ldv, B.V64[0], kp, kp, B.Vh[0], B.Vl[0], &h->launches));
+  // padding rows [M, kp) of the partner BF16 planes must read as zero
+  CHASE_CUDA_TRY(cudaMemsetAsync(B.Vh[1], 0, 2 * (size_t)kp * ncols, st));
+  CHASE_CUDA_TRY(cudaMemsetAsync(B.Vl[1], 0, 2 * (size_t)kp * ncols, st));
+  CHASE_CUDA_TRY(cudaMemsetAsync(&h->dstat->timeout, 0, sizeof(int), st));
+  const int mmax = deg[ncols - 1];
+  const double sigma1 = e / (lambda1 - c);
+  double sigma = sigma1;
+  int first = 0;
+  const double per_col = (Sc<T>::cplx ? 8.0 : 2.0) * (double)n * (double)n;
+  for (int step = 1; step <= mmax; ++step) {
+    while (first < ncols && deg[first] < step) ++first;
+    const int act = ncols - first;
+    const int in = (step % 2 == 1) ? 0 : 1, out = 1 - in;
+    double alpha, beta, gamma;
+    if (step == 1) {
+      alpha = sigma1 / e;
+      beta = -alpha * c;
+      gamma = 0.0;
+    } else {
+      const double sn = 1.0 / (2.0 / sigma1 - sigma);
+      alpha = 2.0 * sn / e;
+      beta = -alpha * c;
+      gamma = -sigma * sn;
+      sigma = sn;
+    }
+    TRY(tc_filter_step(st, M, kp, B.Ah, B.Al, B.Vh[in], B.Vl[in], ncols, first, act, alpha, beta,
+                       B.V64[in], gamma, B.V64[out], B.V64[out], kp, B.Vh[out], B.Vl[out],
+                       h->dstat, &h->launches));
+    if (flops) *flops += per_col * act;
+    if (steps) ++*steps;
+  }
+  // columns ending at an odd step sit in buffer 1, the others in buffer 0
+  int a = 0;
+  while (a < ncols) {
+    int b = a;
+    while (b < ncols && deg[b] == deg[a]) ++b;
+    TRY(tc_unstack_V<T>(st, n, a, b, B.V64[deg[a] % 2], kp, V, ldv, &h->launches));
+    a = b;
+  }
+  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h->hstat->timeout) return CHASE_ERR_TIMEOUT;
+  return 0;
+}
+
 // One CholeskyQR pass (Algorithm 2 body): X <- X R^{-1} with R = chol(X^H X [+ sI]).
 // Result lands in X (via Xtmp).  Returns 0, CHASE_CHOL_FAILED (info in *info) or an error.
 template <class T>
@@ -263,7 +356,8 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
   cudaStream_t st = h->stream;
   const int l = nev + nex;
   const Layout L = layout_for<T>(n, l);
-  TRY(ensure_ws(h, L.total));
+  const bool mixed = (cfg.prec == CHASE_BF16X3);
+  TRY(ensure_ws(h, L.total + (mixed ? tc_bytes<T>(n, l) : 0)));
   TRY(ensure_hbuf(h, sizeof(double) * 4 * (size_t)l + 4096));
   char* base = (char*)h->ws;
   T* V = (T*)(base + L.V);
@@ -280,6 +374,10 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
   double* dw = (double*)(base + L.dw);
   double* dres = (double*)(base + L.dres);
   Scratch scr{base + L.scratch, kScratchBytes};
+  TcBufs tcb;
+  if (mixed) tcb = tc_carve<T>(base + L.total, n, l);
+  bool lowprec = mixed, A_split = false;
+  const double normA_est = std::max(std::fabs(bd.lambda1), std::fabs(bd.b_sup));
   double* hw = h->hbuf;        // l Ritz values
   double* hr = h->hbuf + l;    // l residuals
 
@@ -330,9 +428,22 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     const int nu = l - k;
     // --- filter ---
     phase_begin();
-    rc = filter_inplace<T>(h, n, A, lda, nu, V + (size_t)k * n, n, P, n, deg.data() + k, c, e, mu1,
-                           scr, &S.filter_flops, &S.filter_launches);
-    phase_end(S.t_filter);
+    if (lowprec) {
+      double fl = 0.0, tf = 0.0;
+      rc = filter_mixed<T>(h, n, A, lda, !A_split, nu, V + (size_t)k * n, n, deg.data() + k, c, e,
+                           mu1, tcb, &fl, &S.filter_launches);
+      A_split = true;
+      phase_end(tf);
+      S.t_filter += tf;
+      S.t_filter_lowprec += tf;
+      S.filter_flops += fl;
+      S.filter_flops_lowprec += fl;
+      ++S.n_lowprec_iters;
+    } else {
+      rc = filter_inplace<T>(h, n, A, lda, nu, V + (size_t)k * n, n, P, n, deg.data() + k, c, e,
+                             mu1, scr, &S.filter_flops, &S.filter_launches);
+      phase_end(S.t_filter);
+    }
     if (rc) break;
     for (int a = k; a < l; ++a) matvecs += deg[a];
     // --- condition estimate (Eq. full-est) and QR (Algorithm 3) ---
@@ -398,6 +509,12 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       status = CHASE_OK;
       ++it;
       break;
+    }
+    // mixed mode: FP64 filters once the wanted residuals reach the BF16x3 regime
+    if (lowprec) {
+      double rmax = 0.0;
+      for (int a = k; a < nev; ++a) rmax = std::max(rmax, res[a]);
+      if (rmax <= cfg.mp_switch * normA_est) lowprec = false;
     }
     // --- degrees of the unlocked columns, ascending order ---
     if (cfg.opt_degree) {
@@ -477,8 +594,17 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
 
 template <class T>
 int filter_impl(chase_ctx* h, int n, const T* A, int lda, int ncols, const T* dV, int ldv,
-                const int* degrees, double c, double e, double lambda1, T* dVout, int ldo) {
+                const int* degrees, double c, double e, double lambda1, chase_precision prec,
+                T* dVout, int ldo) {
   cudaStream_t st = h->stream;
+  if (prec == CHASE_BF16X3) {
+    TRY(ensure_ws(h, tc_bytes<T>(n, ncols)));
+    TcBufs B = tc_carve<T>((char*)h->ws, n, ncols);
+    if (dVout != dV) TRY(copy_cols<T>(st, n, ncols, dV, ldv, dVout, ldo, &h->launches));
+    double fl = 0.0;
+    return filter_mixed<T>(h, n, A, lda, true, ncols, dVout, ldo, degrees, c, e, lambda1, B, &fl,
+                           nullptr);
+  }
   const size_t blk = align256(sizeof(T) * (size_t)n * ncols);
   TRY(ensure_ws(h, blk + kScratchBytes));
   T* P = (T*)h->ws;
@@ -535,6 +661,7 @@ int chase_config_default(chase_config* cfg) {
   cfg->cond_lo = 20.0;
   cfg->qr_force = CHASE_QR_AUTO;
   cfg->prec = CHASE_FP64;
+  cfg->mp_switch = 1e-3;
   return CHASE_OK;
 }
 
@@ -584,11 +711,18 @@ int chase_workspace_bytes(chase_dtype dtype, int n, int nev, int nex, chase_prec
   if (n < 1) return -2;
   if (nev < 1) return -3;
   if (nex < 0 || nev + nex > n) return -4;
-  (void)prec;
   if (!bytes) return -6;
-  *bytes = (dtype == CHASE_R64) ? layout_for<double>(n, nev + nex).total
-                                : layout_for<z64>(n, nev + nex).total;
+  const int l = nev + nex;
+  size_t b = (dtype == CHASE_R64) ? layout_for<double>(n, l).total : layout_for<z64>(n, l).total;
+  if (prec == CHASE_BF16X3) b += (dtype == CHASE_R64) ? tc_bytes<double>(n, l) : tc_bytes<z64>(n, l);
+  *bytes = b;
   return CHASE_OK;
+}
+
+int chase_reserve_workspace(chase_handle h, size_t bytes) {
+  if (!h) return -1;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  return ensure_ws(h, bytes);
 }
 
 int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda, int nev, int nex,
@@ -607,7 +741,8 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
   if (!(c.tol > 0.0) || c.max_iter < 0 || c.deg_init < 1 || c.deg_min < 1 || c.deg_max < c.deg_min ||
       !(c.eta > 0.0) || c.qr_force < 0 || c.qr_force > 4)
     return -8;
-  if (c.prec != CHASE_FP64) return CHASE_ERR_UNSUPPORTED;
+  if (c.prec != CHASE_FP64 && c.prec != CHASE_BF16X3) return CHASE_ERR_UNSUPPORTED;
+  if (c.prec == CHASE_BF16X3 && !(c.mp_switch >= 0.0)) return -8;
   if (!bounds || !(bounds->b_sup > bounds->lambda_ell) || !(bounds->lambda_ell >= bounds->lambda1))
     return -9;
   if (!dV) return -10;
@@ -639,16 +774,16 @@ int chase_filter(chase_handle h, chase_dtype dtype, int n, const void* dA, int l
     if (degrees[a] < 0 || (a > 0 && degrees[a] < degrees[a - 1])) return -9;
   if (!(e > 0.0) || !std::isfinite(c)) return -11;
   if (!(lambda1 < c - e)) return -12;
-  if (prec != CHASE_FP64) return CHASE_ERR_UNSUPPORTED;
+  if (prec != CHASE_FP64 && prec != CHASE_BF16X3) return CHASE_ERR_UNSUPPORTED;
   if (ncols > 0 && !dVout) return -14;
   if (ldvout < n) return -15;
   if (ncols == 0) return CHASE_OK;
   if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
   if (dtype == CHASE_R64)
     return filter_impl<double>(h, n, (const double*)dA, lda, ncols, (const double*)dV, ldv, degrees,
-                               c, e, lambda1, (double*)dVout, ldvout);
+                               c, e, lambda1, prec, (double*)dVout, ldvout);
   return filter_impl<z64>(h, n, (const z64*)dA, lda, ncols, (const z64*)dV, ldv, degrees, c, e,
-                          lambda1, (z64*)dVout, ldvout);
+                          lambda1, prec, (z64*)dVout, ldvout);
 }
 
 int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int ldx,

@@ -61,7 +61,7 @@ def known_spectrum_matrix(lam: np.ndarray, seed: int, complex_: bool, device: st
     G = gaussian((n, n), seed, complex_)
     dt = torch.complex128 if complex_ else torch.float64
     Gt = torch.from_numpy(np.ascontiguousarray(G)).to(device=device, dtype=dt)
-    Q, R = torch.linalg.qr(Gt)
+    Q, R = _qr(Gt)
     # fix the phases so that Q does not depend on the QR routine's sign choice
     d = torch.diagonal(R)
     ph = d / d.abs()
@@ -71,6 +71,29 @@ def known_spectrum_matrix(lam: np.ndarray, seed: int, complex_: bool, device: st
     A = 0.5 * (A + A.conj().T)
     del Q, R, Gt
     return A.mT.contiguous().mT
+
+
+def _qr(Gt):
+    """QR of the Gaussian matrix on its device.  torch loads its CUDA linear-algebra
+    library lazily by name; under a profiler's injection that lookup can fail, so the
+    library is preloaded by path first and the CPU is used as a last resort."""
+    import torch
+
+    if Gt.is_cuda:
+        import ctypes
+        import glob
+        import os
+        for lib in glob.glob(os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")):
+            try:
+                ctypes.CDLL(lib, mode=ctypes.RTLD_GLOBAL)
+            except OSError:
+                pass
+        try:
+            return torch.linalg.qr(Gt)
+        except RuntimeError:
+            Q, R = torch.linalg.qr(Gt.cpu())
+            return Q.to(Gt.device), R.to(Gt.device)
+    return torch.linalg.qr(Gt)
 
 
 def start_block(n: int, ell: int, seed: int, complex_: bool) -> np.ndarray:
