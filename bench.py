@@ -34,11 +34,17 @@ METRIC = ("time-to-solution for nev pairs at resid<=1e-10 & filter TFLOP/s vs FP
 # FP64 DFMA peak of GB300 derived from unit counts and the maximum SM clock:
 # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (a DFMA probe measured 1.203 TFLOP/s at ~2.0 GHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Dense BF16 tensor peak measured on the GB300s (cuBLAS, burst), MEASURED_PEAKS.json.
+BF16_PEAK_TFLOPS = 1978.3
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
 # GB300: 114037 filter MatVecs + 8690 Rayleigh-Ritz / residual products over 9 iterations.
 REF_MATVECS_PER_SOLVE = 122727
+
+
+PRECS = {"fp64": lambda P: P.CHASE_FP64, "fp64_emu": lambda P: P.CHASE_FP64_EMU,
+         "bf16x3": lambda P: P.CHASE_BF16X3}
 
 
 def parse():
@@ -58,6 +64,10 @@ def parse():
                          "(kernel-level timing and small cases for profilers)")
     ap.add_argument("--ncols", type=int, default=600, help="filter mode: block width")
     ap.add_argument("--degree", type=int, default=20, help="filter mode: degree of every column")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64_emu", "bf16x3"],
+                    help="A*V arithmetic: fp64 (DFMA), fp64_emu (Ozaki scheme on the BF16 tensor "
+                         "cores, FP64-accurate), bf16x3 (BF16x3 filter while residuals are large, "
+                         "then fp64_emu)")
     return ap.parse_args()
 
 
@@ -80,21 +90,31 @@ def run_filter(args):
     stream = torch.cuda.current_stream()
     h = P.Handle(0, stream=stream.cuda_stream)
     degs = [args.degree] * k
+    prec = PRECS[args.prec](P)
     for _ in range(args.warmup):
-        P.chase_filter(h, A, V, degs, c, e, l1, out=out)
+        P.chase_filter(h, A, V, degs, c, e, l1, out=out, prec=prec)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
-        P.chase_filter(h, A, V, degs, c, e, l1, out=out)
+        P.chase_filter(h, A, V, degs, c, e, l1, out=out, prec=prec)
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / args.steps
     flops = 8.0 * n * n * k * args.degree
     h.close()
-    print(json.dumps({"mode": "filter", "n": n, "ncols": k, "degree": args.degree,
-                      "s_per_filter": t, "tflops": flops / t / 1e12,
-                      "frac_of_fp64_peak": flops / t / 1e12 / FP64_PEAK_TFLOPS}), flush=True)
+    line = {"mode": "filter", "prec": args.prec, "n": n, "ncols": k, "degree": args.degree,
+            "s_per_filter": t, "tflops_fp64_equivalent": flops / t / 1e12}
+    if args.prec == "fp64":
+        line["frac_of_fp64_peak"] = flops / t / 1e12 / FP64_PEAK_TFLOPS
+    else:
+        # BF16 tensor-core products of the stacked real operator (2n x 2n) per step:
+        # 3 for BF16x3, 36 slice pairs for the Ozaki scheme
+        npairs = 3 if args.prec == "bf16x3" else 36
+        tc = npairs * 2.0 * (2 * n) * (2 * n) * k * args.degree / t / 1e12
+        line["bf16_tensor_tflops"] = tc
+        line["frac_of_bf16_peak"] = tc / BF16_PEAK_TFLOPS
+    print(json.dumps(line), flush=True)
 
 
 class ClockSampler:
@@ -213,11 +233,12 @@ def _estimate_matvecs(prob):
 
 
 def _config(args, prob):
+    prec = getattr(args, "prec", "fp64")
     return {"workload": "complex Hermitian n=%d, nev=%d, nex=%d, clustered lowest %d in [-2,-1], "
-                        "rest U[-1,50], degrees 10-36 (init 20), tol 1e-10, FP64 filter"
-                        % (prob.n, prob.nev, prob.nex, prob.ell),
+                        "rest U[-1,50], degrees 10-36 (init 20), tol 1e-10, %s filter"
+                        % (prob.n, prob.nev, prob.nex, prob.ell, prec.upper()),
             "n": prob.n, "nev": prob.nev, "nex": prob.nex, "dtype": "complex128",
-            "precision": "fp64", "l2": "inputs larger than L2 (A is %.1f GB)" % (16 * prob.n ** 2 / 1e9),
+            "precision": prec, "l2": "inputs larger than L2 (A is %.1f GB)" % (16 * prob.n ** 2 / 1e9),
             "parallelism": "replicas (1 problem per GPU)" if args.gpus > 1 else "single GPU"}
 
 
@@ -251,7 +272,8 @@ def main():
     stream = torch.cuda.current_stream()
     h = P.Handle(local, stream=stream.cuda_stream)
     cfg = P.config_default(opt_degree=1, deg_init=prob.deg_init, deg_min=prob.deg_min,
-                           deg_max=prob.deg_max, tol=prob.tol)
+                           deg_max=prob.deg_max, tol=prob.tol,
+                           prec=PRECS[args.prec](P))
     bounds = prob.bounds
 
     def one_solve():
@@ -306,7 +328,12 @@ def main():
         "iterations": st["iterations"], "matvecs": st["matvecs"],
         "qr_variants": {"cholqr1": st["n_chol1"], "cholqr2": st["n_chol2"],
                         "shifted_cholqr2": st["n_shifted"], "householder": st["n_hhqr"]},
-        "phase_s": {k: st[k] for k in ("t_filter", "t_qr", "t_rr", "t_resid", "t_total")},
+        "phase_s": {k: st[k] for k in ("t_filter", "t_qr", "t_rr", "t_resid", "t_total",
+                                        "t_filter_lowprec")},
+        "lowprec_iterations": st["n_lowprec_iters"],
+        "iteration_log": [{"it": g["iteration"], "locked": g["locked_before"],
+                           "variant": g["variant"], "log10_cond_est": g["log_cond_est"] / 2.302585092994046,
+                           "matvecs": g["matvecs"], "deg": [g["deg_min"], g["deg_max"]]} for g in logs],
         "roofline": {"kernel": "gemm_kernel (filter step, FP64 complex, fused 3-term epilogue)",
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,

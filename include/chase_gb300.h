@@ -42,9 +42,16 @@ typedef struct chase_ctx* chase_handle;
 
 typedef enum { CHASE_R64 = 0, CHASE_C128 = 1 } chase_dtype;
 
-/* Arithmetic of the filter's A*V products.  FP64 is exact double precision.
- * The remaining steps (QR, Rayleigh-Ritz, residuals) are always FP64. */
-typedef enum { CHASE_FP64 = 0, CHASE_TF32 = 1, CHASE_BF16X3 = 2 } chase_precision;
+/* Arithmetic of the A*V products (filter and Rayleigh-Ritz).
+ *   CHASE_FP64      native FP64 (DFMA) everywhere.
+ *   CHASE_FP64_EMU  A*V products by the Ozaki scheme on the BF16 tensor cores:
+ *                   8 exact 7-bit slices per operand, exact integer accumulation,
+ *                   accurate to ~2^-53 |A||V| per entry like an FP64 product.
+ *   CHASE_BF16X3    mixed: BF16x3 filter products (three BF16 tensor-core
+ *                   products of hi/lo splits, FP32 accumulation) while the
+ *                   residuals are large, then CHASE_FP64_EMU.
+ * QR, the Rayleigh-Ritz Gram and residuals stay native FP64 in every mode. */
+typedef enum { CHASE_FP64 = 0, CHASE_TF32 = 1, CHASE_BF16X3 = 2, CHASE_FP64_EMU = 3 } chase_precision;
 
 typedef enum {
   CHASE_OK = 0,
@@ -73,7 +80,7 @@ typedef struct {
   double cond_hi;    /* Algorithm 3: shifted CholeskyQR2 above this estimate (1e8) */
   double cond_lo;    /* Algorithm 3: CholeskyQR1 below this estimate (20) */
   int qr_force;      /* CHASE_QR_AUTO or a forced variant */
-  chase_precision prec; /* filter arithmetic: CHASE_FP64, or CHASE_BF16X3 for the mixed mode */
+  chase_precision prec; /* arithmetic of the A*V products (see chase_precision) */
   double mp_switch;  /* mixed mode: the filter runs in BF16x3 until the largest residual of the
                         unlocked wanted pairs drops to mp_switch * max(|lambda1|, |b_sup|),
                         then in FP64 for the remaining iterations (default 1e-3) */
@@ -157,9 +164,10 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
  *   degrees   host, ncols ints, ascending, each >= 0 (0 copies the column).
  *   dV        device n x ncols input (not modified); dVout device n x ncols
  *             output (may equal dV).
- *   prec      CHASE_FP64, or CHASE_BF16X3: each A*V product as three BF16
- *             tensor-core products (hi/lo splits, FP32 accumulation), the
- *             recurrence itself in FP64 (CHASE_TF32: CHASE_ERR_UNSUPPORTED).
+ *   prec      CHASE_FP64, CHASE_FP64_EMU (Ozaki-scheme FP64 products on the
+ *             tensor cores) or CHASE_BF16X3 (each A*V product as three BF16
+ *             tensor-core products of hi/lo splits, FP32 accumulation); the
+ *             recurrence itself is FP64 (CHASE_TF32: CHASE_ERR_UNSUPPORTED).
  */
 int chase_filter(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda, int ncols,
                  const void* dV, int ldv, const int* degrees, double c, double e, double lambda1,

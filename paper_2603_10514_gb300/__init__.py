@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libchase_gb300.so")
 
 CHASE_R64, CHASE_C128 = 0, 1
-CHASE_FP64, CHASE_TF32, CHASE_BF16X3 = 0, 1, 2
+CHASE_FP64, CHASE_TF32, CHASE_BF16X3, CHASE_FP64_EMU = 0, 1, 2, 3
 CHASE_OK, CHASE_NOT_CONVERGED, CHASE_CHOL_FAILED = 0, 1, 2
 CHASE_ERR_CUDA, CHASE_ERR_OOM, CHASE_ERR_TIMEOUT, CHASE_ERR_NONFINITE, CHASE_ERR_UNSUPPORTED = 3, 4, 5, 6, 7
 CHASE_ERR_TOO_LARGE = 8

@@ -84,4 +84,21 @@ int tc_filter_step(cudaStream_t st, int M, int kp, const void* Ah, const void* A
                    double* out64, int ldv, void* Vh_out, void* Vl_out, DevStatus* dst,
                    int* launches);
 
+// ---- FP64-accurate Ozaki-scheme products on BF16 tensor cores (gemm_oz.cu) -
+// 8 BF16 digit planes per operand.  A planes: row-major (M x kp), V planes:
+// column-major (kp x ncols_total).
+template <class T>
+int oz_slice_A(cudaStream_t st, int n, const T* A, int lda, int kp, void* planes, int* rowexp,
+               int* launches);
+int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ldi, int kp,
+               int ncols_total, void* planes, int* colexp, int* launches);
+template <class T>
+int oz_stack_V(cudaStream_t st, int n, int ncols, const T* V, int ldv, double* V64, int ldo,
+               int* launches);
+// out64[:, col0 + c] = alpha * (A V)[:, col0 + c] + beta * X64 + gamma * Z64 for c < N.
+int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
+            const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
+            double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
+            DevStatus* dst, int* launches);
+
 }  // namespace chase

@@ -267,6 +267,105 @@ int filter_mixed(chase_ctx* h, int n, const T* A, int lda, bool split_A, int nco
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// FP64-accurate A*V products by the Ozaki scheme (gemm_oz.cu): digit planes of
+// A (prepared once per call site) and of the current block.
+// ---------------------------------------------------------------------------
+struct OzBufs {
+  int M = 0, kp = 0, ncols = 0;
+  void* Ap = nullptr;
+  int* rowexp = nullptr;
+  void* Vp = nullptr;
+  int* colexp = nullptr;
+  double* V64[2] = {nullptr, nullptr};
+};
+
+template <class T>
+size_t oz_bytes(int n, int ncols) {
+  const int M = Sc<T>::cplx ? 2 * n : n;
+  const size_t kp = (size_t)tc_kpad(M);
+  return align256(16 * (size_t)M * kp) + align256(4 * (size_t)M) + align256(16 * kp * ncols) +
+         align256(4 * (size_t)ncols) + 2 * align256(8 * kp * ncols);
+}
+
+template <class T>
+OzBufs oz_carve(char* base, int n, int ncols) {
+  OzBufs B;
+  B.M = Sc<T>::cplx ? 2 * n : n;
+  B.kp = tc_kpad(B.M);
+  B.ncols = ncols;
+  size_t off = 0;
+  B.Ap = base + off; off += align256(16 * (size_t)B.M * B.kp);
+  B.rowexp = (int*)(base + off); off += align256(4 * (size_t)B.M);
+  B.Vp = base + off; off += align256(16 * (size_t)B.kp * ncols);
+  B.colexp = (int*)(base + off); off += align256(4 * (size_t)ncols);
+  for (int i = 0; i < 2; ++i) { B.V64[i] = (double*)(base + off); off += align256(8 * (size_t)B.kp * ncols); }
+  return B;
+}
+
+template <class T>
+int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols, T* V, int ldv,
+              const int* deg, double c, double e, double lambda1, OzBufs& B, double* flops,
+              int* steps) {
+  cudaStream_t st = h->stream;
+  if (ncols <= 0) return 0;
+  const int M = B.M, kp = B.kp;
+  if (split_A) TRY(oz_slice_A<T>(st, n, A, lda, kp, B.Ap, B.rowexp, &h->launches));
+  TRY(oz_stack_V<T>(st, n, ncols, V, ldv, B.V64[0], kp, &h->launches));
+  CHASE_CUDA_TRY(cudaMemsetAsync(&h->dstat->timeout, 0, sizeof(int), st));
+  const int mmax = deg[ncols - 1];
+  const double sigma1 = e / (lambda1 - c);
+  double sigma = sigma1;
+  int first = 0;
+  const double per_col = (Sc<T>::cplx ? 8.0 : 2.0) * (double)n * (double)n;
+  for (int step = 1; step <= mmax; ++step) {
+    while (first < ncols && deg[first] < step) ++first;
+    const int act = ncols - first;
+    const int in = (step % 2 == 1) ? 0 : 1, out = 1 - in;
+    double alpha, beta, gamma;
+    if (step == 1) {
+      alpha = sigma1 / e;
+      beta = -alpha * c;
+      gamma = 0.0;
+    } else {
+      const double sn = 1.0 / (2.0 / sigma1 - sigma);
+      alpha = 2.0 * sn / e;
+      beta = -alpha * c;
+      gamma = -sigma * sn;
+      sigma = sn;
+    }
+    TRY(oz_slice_V(st, M, first, ncols, B.V64[in], kp, kp, ncols, B.Vp, B.colexp, &h->launches));
+    TRY(oz_gemm(st, M, kp, B.Ap, B.rowexp, B.Vp, B.colexp, ncols, first, act, alpha, beta,
+                B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, &h->launches));
+    if (flops) *flops += per_col * act;
+    if (steps) ++*steps;
+  }
+  int a = 0;
+  while (a < ncols) {
+    int b = a;
+    while (b < ncols && deg[b] == deg[a]) ++b;
+    TRY(tc_unstack_V<T>(st, n, a, b, B.V64[deg[a] % 2], kp, V, ldv, &h->launches));
+    a = b;
+  }
+  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h->hstat->timeout) return CHASE_ERR_TIMEOUT;
+  return 0;
+}
+
+// AQ = A Q (n x nu, both ld n) by the Ozaki-scheme product; A's planes must be ready.
+template <class T>
+int aq_oz(chase_ctx* h, int n, const T* Q, int nu, T* AQ, OzBufs& B) {
+  cudaStream_t st = h->stream;
+  if (nu <= 0) return 0;
+  TRY(oz_stack_V<T>(st, n, nu, Q, n, B.V64[0], B.kp, &h->launches));
+  TRY(oz_slice_V(st, B.M, 0, nu, B.V64[0], B.kp, B.kp, B.ncols, B.Vp, B.colexp, &h->launches));
+  TRY(oz_gemm(st, B.M, B.kp, B.Ap, B.rowexp, B.Vp, B.colexp, B.ncols, 0, nu, 1.0, 0.0, nullptr,
+              0.0, nullptr, B.V64[1], B.kp, h->dstat, &h->launches));
+  TRY(tc_unstack_V<T>(st, n, 0, nu, B.V64[1], B.kp, AQ, n, &h->launches));
+  return 0;
+}
+
 // One CholeskyQR pass (Algorithm 2 body): X <- X R^{-1} with R = chol(X^H X [+ sI]).
 // Result lands in X (via Xtmp).  Returns 0, CHASE_CHOL_FAILED (info in *info) or an error.
 template <class T>
@@ -357,7 +456,9 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
   const int l = nev + nex;
   const Layout L = layout_for<T>(n, l);
   const bool mixed = (cfg.prec == CHASE_BF16X3);
-  TRY(ensure_ws(h, L.total + (mixed ? tc_bytes<T>(n, l) : 0)));
+  const bool emu = (cfg.prec == CHASE_BF16X3 || cfg.prec == CHASE_FP64_EMU);
+  const size_t tcb_bytes = mixed ? tc_bytes<T>(n, l) : 0;
+  TRY(ensure_ws(h, L.total + tcb_bytes + (emu ? oz_bytes<T>(n, l) : 0)));
   TRY(ensure_hbuf(h, sizeof(double) * 4 * (size_t)l + 4096));
   char* base = (char*)h->ws;
   T* V = (T*)(base + L.V);
@@ -376,7 +477,9 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
   Scratch scr{base + L.scratch, kScratchBytes};
   TcBufs tcb;
   if (mixed) tcb = tc_carve<T>(base + L.total, n, l);
-  bool lowprec = mixed, A_split = false;
+  OzBufs ozb;
+  if (emu) ozb = oz_carve<T>(base + L.total + tcb_bytes, n, l);
+  bool lowprec = mixed, A_split = false, A_oz = false;
   const double normA_est = std::max(std::fabs(bd.lambda1), std::fabs(bd.b_sup));
   double* hw = h->hbuf;        // l Ritz values
   double* hr = h->hbuf + l;    // l residuals
@@ -439,6 +542,11 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       S.filter_flops += fl;
       S.filter_flops_lowprec += fl;
       ++S.n_lowprec_iters;
+    } else if (emu) {
+      rc = filter_oz<T>(h, n, A, lda, !A_oz, nu, V + (size_t)k * n, n, deg.data() + k, c, e, mu1,
+                        ozb, &S.filter_flops, &S.filter_launches);
+      A_oz = true;
+      phase_end(S.t_filter);
     } else {
       rc = filter_inplace<T>(h, n, A, lda, nu, V + (size_t)k * n, n, P, n, deg.data() + k, c, e,
                              mu1, scr, &S.filter_flops, &S.filter_launches);
@@ -465,8 +573,14 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     // --- Rayleigh-Ritz on the unlocked columns ---
     phase_begin();
     T* Q2 = V + (size_t)k * n;
-    rc = gemm<T>(st, false, n, nu, n, A, lda, Q2, n, AQ, n, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
-                 scr, false, false, &h->launches);
+    if (emu) {
+      if (!A_oz) rc = oz_slice_A<T>(st, n, A, lda, ozb.kp, ozb.Ap, ozb.rowexp, &h->launches);
+      A_oz = true;
+      if (!rc) rc = aq_oz<T>(h, n, Q2, nu, AQ, ozb);
+    } else {
+      rc = gemm<T>(st, false, n, nu, n, A, lda, Q2, n, AQ, n, 1.0, 0.0, nullptr, 0, 0.0, nullptr,
+                   0, scr, false, false, &h->launches);
+    }
     if (!rc) rc = gemm<T>(st, true, nu, nu, n, Q2, n, AQ, n, H, nu, 1.0, 0.0, nullptr, 0, 0.0,
                           nullptr, 0, scr, true, false, &h->launches);
     if (!rc) rc = herm_fill_lower<T>(st, nu, H, nu, &h->launches);
@@ -597,6 +711,14 @@ int filter_impl(chase_ctx* h, int n, const T* A, int lda, int ncols, const T* dV
                 const int* degrees, double c, double e, double lambda1, chase_precision prec,
                 T* dVout, int ldo) {
   cudaStream_t st = h->stream;
+  if (prec == CHASE_FP64_EMU) {
+    TRY(ensure_ws(h, oz_bytes<T>(n, ncols)));
+    OzBufs B = oz_carve<T>((char*)h->ws, n, ncols);
+    if (dVout != dV) TRY(copy_cols<T>(st, n, ncols, dV, ldv, dVout, ldo, &h->launches));
+    double fl = 0.0;
+    return filter_oz<T>(h, n, A, lda, true, ncols, dVout, ldo, degrees, c, e, lambda1, B, &fl,
+                        nullptr);
+  }
   if (prec == CHASE_BF16X3) {
     TRY(ensure_ws(h, tc_bytes<T>(n, ncols)));
     TcBufs B = tc_carve<T>((char*)h->ws, n, ncols);
@@ -715,6 +837,8 @@ int chase_workspace_bytes(chase_dtype dtype, int n, int nev, int nex, chase_prec
   const int l = nev + nex;
   size_t b = (dtype == CHASE_R64) ? layout_for<double>(n, l).total : layout_for<z64>(n, l).total;
   if (prec == CHASE_BF16X3) b += (dtype == CHASE_R64) ? tc_bytes<double>(n, l) : tc_bytes<z64>(n, l);
+  if (prec == CHASE_BF16X3 || prec == CHASE_FP64_EMU)
+    b += (dtype == CHASE_R64) ? oz_bytes<double>(n, l) : oz_bytes<z64>(n, l);
   *bytes = b;
   return CHASE_OK;
 }
@@ -741,7 +865,8 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
   if (!(c.tol > 0.0) || c.max_iter < 0 || c.deg_init < 1 || c.deg_min < 1 || c.deg_max < c.deg_min ||
       !(c.eta > 0.0) || c.qr_force < 0 || c.qr_force > 4)
     return -8;
-  if (c.prec != CHASE_FP64 && c.prec != CHASE_BF16X3) return CHASE_ERR_UNSUPPORTED;
+  if (c.prec != CHASE_FP64 && c.prec != CHASE_BF16X3 && c.prec != CHASE_FP64_EMU)
+    return CHASE_ERR_UNSUPPORTED;
   if (c.prec == CHASE_BF16X3 && !(c.mp_switch >= 0.0)) return -8;
   if (!bounds || !(bounds->b_sup > bounds->lambda_ell) || !(bounds->lambda_ell >= bounds->lambda1))
     return -9;
@@ -774,7 +899,8 @@ int chase_filter(chase_handle h, chase_dtype dtype, int n, const void* dA, int l
     if (degrees[a] < 0 || (a > 0 && degrees[a] < degrees[a - 1])) return -9;
   if (!(e > 0.0) || !std::isfinite(c)) return -11;
   if (!(lambda1 < c - e)) return -12;
-  if (prec != CHASE_FP64 && prec != CHASE_BF16X3) return CHASE_ERR_UNSUPPORTED;
+  if (prec != CHASE_FP64 && prec != CHASE_BF16X3 && prec != CHASE_FP64_EMU)
+    return CHASE_ERR_UNSUPPORTED;
   if (ncols > 0 && !dVout) return -14;
   if (ldvout < n) return -15;
   if (ncols == 0) return CHASE_OK;

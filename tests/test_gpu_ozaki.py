@@ -1,0 +1,103 @@
+"""FP64-accurate products by the Ozaki scheme on the BF16 tensor cores (CHASE_FP64_EMU),
+through the C ABI.
+
+Tolerances: the emulated product is accurate to ~2^-53 |A||V| per entry (8 slices of
+7 bits = 56 bits of each scaled operand, dropped slice pairs below 2^-63, exact
+integer accumulation), i.e. the same class as an FP64 GEMM; the tests hold it to the
+FP64 tolerances of the parity tests:
+  * one filter step vs FP64 numpy: every entry within the Ozaki bound
+    K 2^-53 max_k|A_mk| max_k|V_kc| (plus 2^-52 for the FP64 recurrence terms), and
+    dense columns within 1e-13 normwise, as an FP64 product;
+  * whole filter vs the oracle: <= 1e-11 (as the native FP64 filter);
+  * solve: eigenvalues within 1e-10 ||A|| of the oracle and of the known spectrum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_10514_gb300 as P
+    P.build()
+    return P
+
+
+@pytest.fixture(scope="module")
+def handle(cl):
+    h = cl.Handle(0)
+    yield h
+    h.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x).T)).cuda().mT
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+@pytest.mark.parametrize("n,ncols", [(333, 37), (517, 70), (1000, 130)])
+def test_one_step_is_fp64_accurate(cl, handle, complex_, n, ncols):
+    lam = W.spectrum_uniform(n, -3.0, 40.0, 3)
+    A = W.known_spectrum_matrix(lam, 3, complex_).numpy()
+    V = W.start_block(n, ncols, 4, complex_)
+    V[:, 1] *= 1e-9          # columns of very different scale
+    V[5, 2] = 1e3            # one large entry
+    c, e, l1 = 20.0, 21.0, -5.0
+    got = cl.chase_filter(handle, dev(A), dev(V), [1] * ncols, c, e, l1,
+                          prec=cl.CHASE_FP64_EMU).cpu().numpy()
+    s = 1.0 / (l1 - c)
+    ref = s * (A @ V - c * V)
+    # Ozaki-scheme error class: each entry of A V within K 2^-53 max_k|A_mk| max_k|V_kc|
+    # (row / column scalings, 56-bit slices), the FP64 recurrence terms within 2^-52
+    K = 2 * n if complex_ else n
+    bound = abs(s) * (K * 2.0 ** -53 * np.abs(A).max(axis=1)[:, None] * np.abs(V).max(axis=0)[None, :]
+                      + abs(c) * np.abs(V) * 2.0 ** -52)
+    ratio = np.abs(got - ref) / bound
+    assert ratio.max() <= 1.0, ratio.max()
+    # and dense columns (all but the two rescaled ones) are as accurate as an FP64 product
+    dense = [j for j in range(ncols) if j not in (1, 2)]
+    err = np.linalg.norm((got - ref)[:, dense], axis=0) / np.linalg.norm(ref[:, dense], axis=0)
+    assert err.max() <= 1e-13, err.max()
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_filter_matches_oracle_fp64_tolerance(cl, handle, complex_):
+    n = 517
+    degs = [0, 1, 2, 2, 5, 8, 8, 13, 20, 20, 27, 36] + [36] * 60
+    lam = W.spectrum_clustered(n, 100, 6) if complex_ else W.spectrum_uniform(n, -1, 1, 6)
+    A = W.known_spectrum_matrix(lam, 6, complex_).numpy()
+    V = W.start_block(n, len(degs), 7, complex_)
+    l1, le, bs = lam[0], lam[len(degs) - 1], lam[-1] + 1e-3
+    c, e = 0.5 * (bs + le), 0.5 * (bs - le)
+    ref = oracle.filter(A, V, degs, c, e, l1)
+    got = cl.chase_filter(handle, dev(A), dev(V), degs, c, e, l1, prec=cl.CHASE_FP64_EMU).cpu().numpy()
+    err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert err.max() <= 1e-11, err.max()
+
+
+@pytest.mark.parametrize("prec_name", ["CHASE_FP64_EMU", "CHASE_BF16X3"])
+def test_solve_with_emulated_fp64_matches_oracle(cl, handle, prec_name):
+    prob = W.c2_complex_clustered(n=1200, nev=40, nex=12, seed=8)
+    A_t = W.known_spectrum_matrix(prob.lam, prob.seed, True, device="cuda")
+    A = A_t.cpu().numpy()
+    V0 = W.start_block(prob.n, prob.ell, prob.seed, True)
+    l1, le, bs = prob.bounds
+    ref = oracle.solve(A, V0, prob.nev, prob.nex, opt_degree=True, lambda1=l1, lambda_ell=le, b_sup=bs)
+    cfg = cl.config_default(opt_degree=1, prec=getattr(cl, prec_name))
+    rc, ev, res, st, logs = cl.chase_solve(handle, A_t, dev(V0), prob.nev, prob.nex, prob.bounds, cfg)
+    normA = np.abs(prob.lam).max()
+    assert rc == 0
+    assert res.max() < prob.tol
+    assert np.abs(ev - ref["evals"]).max() <= 1e-10 * normA
+    assert np.abs(ev - prob.lam[:prob.nev]).max() <= 1e-10 * normA
+    if prec_name == "CHASE_FP64_EMU":
+        assert abs(st["iterations"] - ref["summary"]["iterations"]) <= 1
+        assert abs(st["matvecs"] - ref["summary"]["matvecs"]) <= 0.05 * ref["summary"]["matvecs"]
