@@ -11,12 +11,15 @@
 //   (A V)[m, c] = 2^{e_m + f_c} sum_{t=2}^{9} 2^{-7t} L_t[m, c],
 //   L_t = sum_{i + j = t} A_i V_j        (pairs with i + j > 9 are dropped:
 //                                         their weight is below 2^-63),
-// 36 BF16 products per output.  Each L_t is an integer; over a K chunk of
-// 128 its partial sum is bounded by 8 * 128 * 127^2 < 2^24, so the tensor
-// core's FP32 accumulation is exact.  After every chunk the epilogue adds the
-// eight level sums into two int64 accumulators per output (levels 2..5 and
-// 6..9, each level shifted into place), which stay exact over the whole K.
-// The result is A*V to within ~2^-53 of |A| |V| per entry, like an FP64 GEMM.
+// 36 BF16 products per output.  Levels 2..5 carry the leading bits and must
+// be summed exactly: each is an integer whose partial sum over a K chunk of
+// 256 is bounded by 4 * 256 * 127^2 < 2^24, so the tensor core's FP32
+// accumulation is exact; after every chunk the epilogue adds them, shifted
+// into place, into one int64 per output, which stays exact over the whole K.
+// Levels 6..9 weigh at most 2^-28 of level 2, so FP32 accumulation over the
+// whole K (relative rounding 2^-24) keeps their error below 2^-52 of the
+// result; they are read once at the end.  The result is A*V to within
+// ~2^-53 K max|A_m.| max|V_.c| per entry, the accuracy class of an FP64 GEMM.
 //
 // Kernel: one CTA per 128 x 64 output tile, 320 threads:
 //   warp 0     TMA producer: per 64-wide K block, the 8 V digit tiles
@@ -24,9 +27,10 @@
 //              tiles (128 x 64 BF16) streamed through a 4-deep ring;
 //   warp 1     allocates all 512 TMEM columns (8 levels x 64) and issues the
 //              tcgen05.mma.kind::f16 (M 128, N 64, K 16): 144 per K block;
-//   warps 2-9  epilogue: per chunk, tcgen05.ld of 8 levels for 32 rows x 32
-//              columns, exact int64 accumulation; at the end the FP64
-//              recombination and the Chebyshev three-term update.
+//   warps 2-9  epilogue: per 256-wide chunk, tcgen05.ld of levels 2..5 for 32
+//              rows x 32 columns and exact int64 accumulation; at the end
+//              levels 6..9, the FP64 recombination and the Chebyshev
+//              three-term update.
 // All mbarrier waits are bounded; on expiry the kernel records the failure in
 // the device status word, frees its TMEM and returns.
 #include <cuda.h>
@@ -46,7 +50,7 @@ constexpr int OZ_S = 8;          // digits per entry
 constexpr int OZ_B = 7;          // bits per digit
 constexpr int OZ_LEVELS = 8;     // t = 2 .. 9
 constexpr int OBM = 128, OBN = 64, OBK = 64;
-constexpr int OZ_CHUNK_KB = 2;   // 2 K blocks = 128 K per exact chunk
+constexpr int OZ_CHUNK_KB = 4;   // 4 K blocks = 256 K per exact chunk (levels 2..5)
 constexpr int OA_RING = 4;
 constexpr int A_TILE = OBM * OBK * 2;          // 16 KB
 constexpr int V_TILE = OBN * OBK * 2;          // 8 KB
@@ -210,8 +214,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < OBK / 16; ++kk) {
             const uint64_t off = (uint64_t)((kk * 32) >> 4);
-            const uint32_t acc = (chunk_start && i == 1 && kk == 0) ? 0u : 1u;
-            mma(dcol, da + off, dv + off, acc);
+            // levels 2..5 restart every chunk, levels 6..9 accumulate over all of K;
+            // pair (1, t-1) is the first product of level t in each pass
+            const bool restart = (i == 1 && kk == 0) && (t <= 5 ? chunk_start : kb == 0);
+            mma(dcol, da + off, dv + off, restart ? 0u : 1u);
           }
         }
         commit(&aempty[as]);
@@ -224,44 +230,55 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ---------------- epilogue ----------------
     const int q = warp & 3;            // TMEM lane quarter this warp may access
     const int hc = (warp - 2) >> 2;    // column half of the 64-wide tile
-    long long g1[32], g2[32];
+    const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(hc * 32);
+    long long g1[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) { g1[j] = 0; g2[j] = 0; }
+    for (int j = 0; j < 32; ++j) g1[j] = 0;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
       if (!bar_wait(cfull, (uint32_t)(c & 1))) { ok = false; atomicOr(s_err, 4); break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-      for (int t = 2; t <= OZ_S + 1; ++t) {
+      for (int t = 2; t <= 5; ++t) {
         uint32_t r[32];
-        ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((t - 2) * OBN + hc * 32), r);
-        const long long sh = (t <= 5) ? (1LL << (OZ_B * (5 - t))) : (1LL << (OZ_B * (9 - t)));
-        if (t <= 5) {
+        ld32(tbase + (uint32_t)((t - 2) * OBN), r);
+        const long long sh = 1LL << (OZ_B * (5 - t));
 #pragma unroll
-          for (int j = 0; j < 32; ++j) g1[j] += (long long)__float2int_rz(__uint_as_float(r[j])) * sh;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) g2[j] += (long long)__float2int_rz(__uint_as_float(r[j])) * sh;
-        }
+        for (int j = 0; j < 32; ++j) g1[j] += (long long)__float2int_rz(__uint_as_float(r[j])) * sh;
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) bar_arrive(cfree);
+      if (lane == 0 && c + 1 < nchunks) bar_arrive(cfree);
     }
     const int r = m0 + 32 * q + lane;
-    if (ok && r < M && !*(volatile int*)s_err) {
-      const int er = rowexp[r];
+    if (ok && !*(volatile int*)s_err) {
+      // levels 6..9 (FP32 over the whole K), combined with level sum 2..5 in FP64
+      double y[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) y[j] = 0.0;
+#pragma unroll 1
+      for (int t = 9; t >= 6; --t) {
+        uint32_t rr[32];
+        ld32(tbase + (uint32_t)((t - 2) * OBN), rr);
+        const double w = ldexp(1.0, -OZ_B * (t - 5));  // relative to the 2..5 sum's unit
+#pragma unroll
+        for (int j = 0; j < 32; ++j) y[j] = fma((double)__uint_as_float(rr[j]), w, y[j]);
+      }
+      if (r < M) {
+        const int er = rowexp[r];
 #pragma unroll 4
-      for (int j = 0; j < 32; ++j) {
-        const int c = n0 + hc * 32 + j;
-        if (c >= N) break;
-        const int e = er + colexp[col0 + c];
-        const double y = ldexp((double)g1[j], e - 35) + ldexp((double)g2[j], e - 63);
-        const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
-        double v = alpha * y;
-        if (beta != 0.0) v = fma(beta, X64[idx], v);
-        if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
-        out64[idx] = v;
+        for (int j = 0; j < 32; ++j) {
+          const int c = n0 + hc * 32 + j;
+          if (c >= N) break;
+          const int e = er + colexp[col0 + c];
+          // value = 2^{e} 2^{-35} (G1 + sum_{t>=6} 2^{-7(t-5)} L_t)
+          const double v0 = ldexp((double)g1[j] + y[j], e - OZ_B * 5);
+          const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
+          double v = alpha * v0;
+          if (beta != 0.0) v = fma(beta, X64[idx], v);
+          if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
+          out64[idx] = v;
+        }
       }
     }
   }

@@ -27,6 +27,12 @@ int gemm(cudaStream_t st, bool transA, int M, int N, int K, const T* A, int lda,
 template <class T>
 int potrf_upper(cudaStream_t st, int n, T* G, int ldg, double shift_factor, DevStatus* dst,
                 int* launches);
+// Blocked (64) variant for larger n: diagonal blocks on one CTA, block rows and
+// trailing updates as products.  scratch: 64*64 + 64*n elements; the strict lower
+// triangle of G is left as it was.
+template <class T>
+int potrf_upper_blocked(cudaStream_t st, int n, T* G, int ldg, double shift_factor, DevStatus* dst,
+                        T* scratch, Scratch gscr, int* launches);
 // Rinv = R^{-1} for upper-triangular R (zero strict lower part written).
 template <class T>
 int trtri_upper(cudaStream_t st, int n, const T* R, int ldr, T* Rinv, int ldri, int* launches);

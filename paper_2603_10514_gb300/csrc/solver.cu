@@ -375,7 +375,10 @@ int cholqr_pass(chase_ctx* h, int n, int l, T* X, int ldx, T* Xtmp, T* G, T* Ri,
   TRY(gemm<T>(st, true, l, l, n, X, ldx, X, ldx, G, l, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, scr,
               true, false, &h->launches));
   CHASE_CUDA_TRY(cudaMemsetAsync(&h->dstat->chol_info, 0, sizeof(int), st));
-  TRY(potrf_upper<T>(st, l, G, l, shift_factor, h->dstat, &h->launches));
+  if (l > 128)
+    TRY(potrf_upper_blocked<T>(st, l, G, l, shift_factor, h->dstat, Ri, scr, &h->launches));
+  else
+    TRY(potrf_upper<T>(st, l, G, l, shift_factor, h->dstat, &h->launches));
   CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   CHASE_CUDA_TRY(cudaStreamSynchronize(st));
   *info = h->hstat->chol_info;

@@ -252,3 +252,24 @@ def test_solve_rejects_nonfinite(cl, handle):
     A[3, 5] = np.nan
     rc, *_ = cl.chase_solve(handle, dev(A), dev(np.ones((n, 4))), 2, 2, (-1.0, 0.0, 2.0), check=False)
     assert rc == cl.CHASE_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+@pytest.mark.parametrize("l,log10k", [(200, 3), (330, 6), (330, 12)])
+def test_qr_blocked_cholesky_paths(cl, handle, complex_, l, log10k):
+    """Blocks wider than 128 columns use the blocked Cholesky (64-wide diagonal blocks,
+    ragged last block): CholQR2 / shifted CholQR2 results stay orthonormal and agree
+    with the oracle where the factor is unique."""
+    n = 1500
+    X = sv_matrix(n, l, np.logspace(0, -log10k, l), 90 + l, complex_)
+    force = 2 if log10k <= 6 else 3
+    Qo, vo, io = oracle.qr_dynamic(X, 0.0, force=force)
+    Xd = dev(X)
+    rc, v, info = cl.chase_qr(handle, Xd, 1.0, qr_force=force)
+    Q = host(Xd)
+    assert rc == 0 and v == force and info == 0 and io == 0
+    assert _orth(Q) <= 1e-12
+    if log10k <= 6:
+        assert np.abs(Q - Qo).max() <= 1e-8
+    R = Q.conj().T @ X
+    assert np.linalg.norm(np.tril(R, -1)) <= 1e-10 * np.linalg.norm(X)
