@@ -36,6 +36,7 @@ METRIC = ("time-to-solution for nev pairs at resid<=1e-10 & filter TFLOP/s vs FP
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Dense BF16 tensor peak measured on the GB300s (cuBLAS, burst), MEASURED_PEAKS.json.
 BF16_PEAK_TFLOPS = 1978.3
+BF16_SUSTAINED_TFLOPS = 1717.0
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
@@ -43,6 +44,10 @@ BF16_PEAK_TFLOPS = 1978.3
 REF_MATVECS_PER_SOLVE = 122727
 
 
+DTYPES = {"fp64": "f64 (complex128, DFMA)",
+          "fp64_emu": "f64 (complex128; A*V by the Ozaki scheme on bf16 tensor cores, exact "
+                      "integer accumulation; QR/RR/residuals f64)",
+          "bf16x3": "bf16x3 filter with f32 accumulation, then f64-emulated filter; f64 QR/RR"}
 PRECS = {"fp64": lambda P: P.CHASE_FP64, "fp64_emu": lambda P: P.CHASE_FP64_EMU,
          "bf16x3": lambda P: P.CHASE_BF16X3}
 
@@ -64,7 +69,7 @@ def parse():
                          "(kernel-level timing and small cases for profilers)")
     ap.add_argument("--ncols", type=int, default=600, help="filter mode: block width")
     ap.add_argument("--degree", type=int, default=20, help="filter mode: degree of every column")
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64_emu", "bf16x3"],
+    ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "bf16x3"],
                     help="A*V arithmetic: fp64 (DFMA), fp64_emu (Ozaki scheme on the BF16 tensor "
                          "cores, FP64-accurate), bf16x3 (BF16x3 filter while residuals are large, "
                          "then fp64_emu)")
@@ -233,7 +238,7 @@ def _estimate_matvecs(prob):
 
 
 def _config(args, prob):
-    prec = getattr(args, "prec", "fp64")
+    prec = getattr(args, "prec", "fp64_emu")
     return {"workload": "complex Hermitian n=%d, nev=%d, nex=%d, clustered lowest %d in [-2,-1], "
                         "rest U[-1,50], degrees 10-36 (init 20), tol 1e-10, %s filter"
                         % (prob.n, prob.nev, prob.nex, prob.ell, prec.upper()),
@@ -312,18 +317,39 @@ def main():
     rc, ev, res, st, logs = results[-1]
     value = world * args.steps / total
     launches = sum(r[3]["kernel_launches"] for r in results)
-    # roofline of the dominant kernel (the filter's FP64 product with the fused recurrence)
-    fl_launch = st["filter_flops"] / max(1, st["filter_launches"])
-    dur_launch = st["t_filter"] / max(1, st["filter_launches"])
-    achieved = fl_launch / dur_launch / 1e12 if dur_launch > 0 else None
+    # roofline of the dominant kernel: the filter product (CUDA-event time of the filter phase,
+    # which is almost all product launches, divided by the launch count)
+    nl = max(1, st["filter_launches"])
+    dur_launch = st["t_filter"] / nl
+    if args.prec == "fp64":
+        fl_launch = st["filter_flops"] / nl
+        achieved = fl_launch / dur_launch / 1e12 if dur_launch > 0 else None
+        roof = {"kernel": "gemm_kernel (FP64 DFMA filter product, fused three-term epilogue)",
+                "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz", "traffic": None}
+    else:
+        # BF16 tensor work: 36 slice products per FP64-equivalent flop pair for the Ozaki
+        # product, 3 for the BF16x3 filter iterations
+        lp = st["filter_flops_lowprec"]
+        tc_flops = 36.0 * (st["filter_flops"] - lp) + 3.0 * lp
+        achieved = tc_flops / nl / dur_launch / 1e12 if dur_launch > 0 else None
+        roof = {"kernel": "oz_gemm_kernel (Ozaki-scheme FP64 product on BF16 tcgen05)" +
+                          (" + tc_filter_bf16x3_kernel" if lp > 0 else ""),
+                "bound": "tensor", "achieved": achieved, "peak": BF16_SUSTAINED_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / BF16_SUSTAINED_TFLOPS if achieved else None,
+                "peak_source": "measured: cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
+                "traffic": None}
+    fp64_equiv = st["filter_flops"] / st["t_filter"] / 1e12 if st["t_filter"] > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.prec], "data": "synthetic",
         "config": _config(args, prob),
         "time_to_solution_s": {"mean": total / args.steps, "p50": statistics.median(step_s),
                                "p99": max(step_s)},
-        "filter_tflops": achieved,
+        "filter_tflops": fp64_equiv,
+        "filter_frac_of_fp64_peak": fp64_equiv / FP64_PEAK_TFLOPS if fp64_equiv else None,
         "converged": ok, "max_abs_eval_err_vs_known": eval_err, "max_resid": float(res.max()),
         "iterations": st["iterations"], "matvecs": st["matvecs"],
         "qr_variants": {"cholqr1": st["n_chol1"], "cholqr2": st["n_chol2"],
@@ -334,11 +360,7 @@ def main():
         "iteration_log": [{"it": g["iteration"], "locked": g["locked_before"],
                            "variant": g["variant"], "log10_cond_est": g["log_cond_est"] / 2.302585092994046,
                            "matvecs": g["matvecs"], "deg": [g["deg_min"], g["deg_max"]]} for g in logs],
-        "roofline": {"kernel": "gemm_kernel (filter step, FP64 complex, fused 3-term epilogue)",
-                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
-                     "traffic": None},
+        "roofline": roof,
         "gpu_launches": launches,
         "clocks": clocks,
     }
