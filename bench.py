@@ -64,9 +64,17 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=8)
-    ap.add_argument("--mode", default="solve", choices=["solve", "filter"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "sequence", "serve"],
                     help="solve: the headline time-to-solution; filter: chase_filter alone "
-                         "(kernel-level timing and small cases for profilers)")
+                         "(kernel-level timing and small cases for profilers); sequence: 20 "
+                         "correlated real problems with warm starts; serve: a stream of "
+                         "requests through the continuous-batching service")
+    ap.add_argument("--seq-len", type=int, default=20)
+    ap.add_argument("--serve-count", type=int, default=256)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="Poisson arrival rate (requests/s); 0 = measure the saturated "
+                         "throughput first and use 0.8 of it")
     ap.add_argument("--ncols", type=int, default=600, help="filter mode: block width")
     ap.add_argument("--degree", type=int, default=20, help="filter mode: degree of every column")
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "bf16x3"],
@@ -199,6 +207,126 @@ def oracle_sample(A_host, prob, cols, deg=2):
     return dt / (cols * deg), dt
 
 
+def run_sequence(args):
+    """SCF-like sequence: A_0 real symmetric (n = 8000, lambda uniform in [-1, 1]),
+    A_{k+1} = A_k + 1e-3 (G + G^T)/(2 sqrt n); each problem (nev 400, nex 80) is
+    warm-started from the previous problem's final block.  All matrices are generated
+    and resident before the timed region; the timed region is the whole chain."""
+    import numpy as np
+    import torch
+
+    import paper_2603_10514_gb300 as P
+    import workloads as W
+    P.build()
+    n = args.n if args.n != 10000 else 8000
+    nev = args.nev if args.nev != 500 else 400
+    nex = args.nex if args.nex != 100 else 80
+    prob = W.c4_sequence_base(n=n, nev=nev, nex=nex, seed=4)
+    As = [W.known_spectrum_matrix(prob.lam, prob.seed, False, device="cuda")]
+    g = torch.Generator(device="cuda").manual_seed(4)
+    for k in range(1, args.seq_len):
+        G = torch.randn(n, n, generator=g, device="cuda", dtype=torch.float64)
+        E = 1e-3 * (G + G.T) / (2.0 * n ** 0.5)
+        As.append((As[-1] + E).mT.contiguous().mT)
+        del G, E
+    V0 = torch.from_numpy(np.ascontiguousarray(W.start_block(n, prob.ell, 4, False).T)).cuda().mT
+    stream = torch.cuda.current_stream()
+    h = P.Handle(0, stream=stream.cuda_stream)
+    cfg = P.config_default(opt_degree=1, prec=PRECS[args.prec](P))
+    l1, le, bs = prob.bounds
+
+    def chain():
+        V = V0.clone()
+        out = []
+        lam1 = l1
+        for k, A in enumerate(As):
+            bounds = (lam1, le, bs + 3e-3 * k)
+            rc, ev, res, st, _ = P.chase_solve(h, A, V, prob.nev, prob.nex, bounds, cfg)
+            out.append((rc, float(res.max()), st["iterations"], st["matvecs"]))
+            lam1 = float(ev[0]) - 1e-2
+        return out
+
+    chain()  # warm-up (workspace, code paths)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    res = chain()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    h.close()
+    print(json.dumps({"mode": "sequence", "prec": args.prec, "n": n, "nev": nev, "nex": nex,
+                      "problems": len(As), "seconds": t, "problems_per_s": len(As) / t,
+                      "all_converged": all(r[0] == 0 and r[1] < 1e-10 for r in res),
+                      "iterations": [r[2] for r in res], "matvecs": [r[3] for r in res]}), flush=True)
+
+
+def run_serve(args):
+    """Serving stream: requests with n log-uniform in [500, 8000], real / complex 50/50,
+    nev = 5% of n, nex = nev/5, lambda uniform in [-1, 1], Poisson arrivals at a fixed
+    seed, admitted by HBM footprint onto concurrent solver slots."""
+    import numpy as np
+    import torch
+
+    import paper_2603_10514_gb300 as P
+    import workloads as W
+    from paper_2603_10514_gb300.serve import Request, Server, latency_stats
+    P.build()
+    specs = W.serving_stream(count=args.serve_count, seed=5)
+    mats = []
+    for s_ in specs:
+        lam = W.spectrum_uniform(s_["n"], -1.0, 1.0, s_["seed"])
+        A = W.known_spectrum_matrix(lam, s_["seed"], s_["complex"], device="cuda")
+        V0 = W.start_block(s_["n"], s_["nev"] + s_["nex"], s_["seed"], s_["complex"])
+        V0 = torch.from_numpy(np.ascontiguousarray(V0.T)).cuda().mT
+        mats.append((s_, lam, A, V0))
+    cfg = P.config_default(opt_degree=1, prec=PRECS[args.prec](P))
+    import ctypes
+    b = ctypes.c_size_t()
+    P.lib().chase_workspace_bytes(P.CHASE_C128, 8000, 400, 80, PRECS[args.prec](P), ctypes.byref(b))
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.85 * free) - args.serve_slots * b.value
+
+    def run(rate, seed):
+        srv = Server(slots=args.serve_slots, hbm_budget=budget,
+                     make_handle=lambda i: P.Handle(0), slot_workspace=b.value)
+        rng = np.random.default_rng(seed)
+        reqs = []
+        t0 = time.perf_counter()
+        t_next = 0.0
+        for (s_, lam, A, V0) in mats:
+            if rate > 0:
+                t_next += rng.exponential(1.0 / rate)
+                delay = t0 + t_next - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            req = Request(rid=s_["id"], A=A, V0=V0.clone(), nev=s_["nev"], nex=s_["nex"],
+                          bounds=W.bounds_for(lam, s_["nev"] + s_["nex"]), cfg=cfg)
+            reqs.append((srv.submit(req), lam))
+        srv.drain()
+        wall = time.perf_counter() - t0
+        inflight = srv.max_in_flight
+        srv.close()
+        ok = all(r.status == 0 and float(np.max(r.resid)) < 1e-10 and
+                 float(np.abs(r.evals - lam[:r.nev]).max()) <= 1e-10 for r, lam in reqs)
+        return [r for r, _ in reqs], wall, ok, inflight
+
+    if args.serve_rate > 0:
+        rate = args.serve_rate
+        sat = None
+    else:
+        _, wall_sat, _, _ = run(0.0, 0)
+        sat = len(mats) / wall_sat
+        rate = 0.8 * sat
+    reqs, wall, ok, inflight = run(rate, 5)
+    lat = latency_stats(reqs)
+    print(json.dumps({"mode": "serve", "prec": args.prec, "requests": len(reqs),
+                      "slots": args.serve_slots, "arrival_rate_per_s": rate,
+                      "saturated_solves_per_s": sat, "solves_per_s": len(reqs) / wall,
+                      "wall_s": wall, "latency": lat, "all_correct": ok,
+                      "max_in_flight": inflight}), flush=True)
+
+
 def run_reference(args, rank):
     """The oracle arm: the CPU oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
@@ -257,6 +385,12 @@ def main():
         return
     if args.mode == "filter":
         run_filter(args)
+        return
+    if args.mode == "sequence":
+        run_sequence(args)
+        return
+    if args.mode == "serve":
+        run_serve(args)
         return
     import numpy as np
     import torch

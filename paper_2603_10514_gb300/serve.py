@@ -2,15 +2,16 @@
 
 Requests (dense Hermitian / symmetric eigenproblems of different orders) arrive at
 any time.  A request is admitted as soon as a solver slot is idle and its HBM
-footprint (A, the search block and the solver workspace) fits in the memory that
-admitted requests leave free; admission is first-come-first-served with backfill
-(a smaller later request may start while a large one at the head of the queue
-waits for memory).  Each slot owns a chase handle with its own CUDA stream and a
-workspace sized once, at start-up, for the largest admissible problem, so that
-no device allocation happens while requests are in flight.  Admitted requests
-run concurrently: their kernels overlap on the device through the slots'
-streams, and a request's result does not depend on what else is running (every
-kernel's arithmetic order is fixed by the problem's shape only).
+footprint fits in the memory left by the requests in flight; admission is
+first-come-first-served with backfill (a smaller later request may start while a
+larger one at the head of the queue waits for memory).  Each slot owns a chase
+handle with its own CUDA stream, and its workspace is reserved once at start-up for
+the largest admissible problem, so that no device allocation happens while
+requests run.  Admitted requests run concurrently: their kernels overlap on the
+device through the slots' streams.  A request's result does not depend on what
+else is running, because every kernel's arithmetic order is fixed by the problem's
+own shape (split-K reductions in a fixed order, exact integer accumulation in the
+tensor-core products).
 
 Latency of a request = completion time - arrival time (queueing included).
 """
@@ -23,14 +24,12 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (CHASE_C128, CHASE_R64, Handle, chase_solve, config_default, lib)
-
 
 @dataclass
 class Request:
     rid: int
-    A: object              # column-major CUDA tensor (float64 / complex128)
-    V0: object             # column-major CUDA tensor, n x (nev + nex)
+    A: object              # column-major CUDA tensor (float64 / complex128), resident
+    V0: object             # column-major CUDA tensor n x (nev + nex), overwritten by the solve
     nev: int
     nex: int
     bounds: tuple
@@ -42,6 +41,7 @@ class Request:
     evals: np.ndarray = None
     resid: np.ndarray = None
     stats: dict = None
+    slot: int = -1
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -49,114 +49,117 @@ class Request:
         return self.A.shape[0]
 
     def footprint(self):
-        import ctypes
-        dt = CHASE_C128 if self.A.is_complex() else CHASE_R64
-        b = ctypes.c_size_t()
-        rc = lib().chase_workspace_bytes(dt, self.n, self.nev, self.nex, 0, ctypes.byref(b))
-        if rc:
-            raise ValueError("invalid request shape")
+        """Device bytes the request occupies while in flight besides the slot's reserved
+        workspace: its matrix and its search block."""
         esz = self.A.element_size()
-        # the workspace is pre-reserved per slot; the request's own device memory is its
-        # search block (A is already resident when the request arrives)
-        return b.value, esz * self.n * (self.nev + self.nex)
+        return esz * self.n * self.n + esz * self.n * (self.nev + self.nex)
 
 
 class Server:
-    """Runs requests on `slots` concurrent solver slots of one GPU."""
+    """Runs requests on `slots` concurrent solver slots.
 
-    def __init__(self, device=0, slots=4, max_n=8000, max_ell=480, complex_=True,
-                 hbm_budget=None):
-        import torch
-        self.device = device
-        torch.cuda.set_device(device)
-        self.handles = [Handle(device) for _ in range(slots)]
-        # size every slot's workspace once for the largest admissible problem
-        import ctypes
-        b = ctypes.c_size_t()
-        lib().chase_workspace_bytes(CHASE_C128 if complex_ else CHASE_R64, max_n,
-                                    max(1, max_ell - max_ell // 6), max_ell // 6, 0, ctypes.byref(b))
-        self.slot_ws = b.value
-        self.max_n = max_n
-        self._warm(max_n, max_ell, complex_)
-        free, _ = torch.cuda.mem_get_info(device)
-        self.budget = hbm_budget if hbm_budget is not None else int(0.9 * free)
+    solve_fn(slot, request) -> (status, evals, resid, stats) performs one solve; the
+    default uses the slot's chase handle (created by `make_handle(slot)`)."""
+
+    def __init__(self, slots=4, hbm_budget=1 << 62, solve_fn=None, make_handle=None,
+                 slot_workspace=0):
+        self.nslots = slots
+        self.handles = [make_handle(i) for i in range(slots)] if make_handle else [None] * slots
+        if slot_workspace:
+            for h in self.handles:
+                h.reserve(slot_workspace)
+        self.solve_fn = solve_fn or self._chase_solve
+        self.budget = hbm_budget
         self.in_use = 0
         self.queue = collections.deque()
         self.idle = collections.deque(range(slots))
-        self.lock = threading.Condition()
-        self.stop = False
+        self.cv = threading.Condition()
+        self.closing = False
         self.completed = []
-        self.threads = []
+        self.workers = []
+        self.max_in_flight = 0
         self.sched = threading.Thread(target=self._schedule, daemon=True)
         self.sched.start()
 
-    def _warm(self, max_n, max_ell, complex_):
-        """Grow each handle's workspace to the largest admissible size now, so that no
-        device allocation happens while requests run."""
-        for h in self.handles:
-            h.reserve(self.slot_ws)
+    # -- default solver -------------------------------------------------------
+    def _chase_solve(self, slot, req):
+        from . import chase_solve
+        rc, ev, res, st, _ = chase_solve(self.handles[slot], req.A, req.V0, req.nev, req.nex,
+                                         req.bounds, req.cfg, check=False)
+        return rc, ev, res, st
 
+    # -- client side ----------------------------------------------------------
     def submit(self, req: Request):
         req.t_arrive = time.perf_counter()
-        with self.lock:
+        with self.cv:
+            if req.footprint() > self.budget:
+                raise ValueError("request %d needs more memory than the whole budget" % req.rid)
             self.queue.append(req)
-            self.lock.notify_all()
+            self.cv.notify_all()
         return req
 
-    def _schedule(self):
-        while True:
-            with self.lock:
-                while not self.stop and not self._admit_one():
-                    self.lock.wait(timeout=0.05)
-                if self.stop and not self.queue:
-                    return
-
-    def _admit_one(self):
-        if not self.queue or not self.idle:
-            return False
-        for i, req in enumerate(self.queue):
-            _, need = req.footprint()
-            if self.in_use + need <= self.budget and req.n <= self.max_n:
-                del self.queue[i]
-                slot = self.idle.popleft()
-                self.in_use += need
-                req.t_admit = time.perf_counter()
-                t = threading.Thread(target=self._run, args=(slot, req, need), daemon=True)
-                self.threads.append(t)
-                t.start()
-                return True
-        return False
-
-    def _run(self, slot, req, need):
-        h = self.handles[slot]
-        try:
-            rc, ev, res, st, _ = chase_solve(h, req.A, req.V0, req.nev, req.nex, req.bounds,
-                                             req.cfg, check=False)
-            req.status, req.evals, req.resid, req.stats = rc, ev, res, st
-        finally:
-            req.t_done = time.perf_counter()
-            with self.lock:
-                self.in_use -= need
-                self.idle.append(slot)
-                self.completed.append(req)
-                self.lock.notify_all()
-            req.done.set()
-
     def drain(self):
-        with self.lock:
-            self.stop = True
-            self.lock.notify_all()
+        """Wait until every submitted request has completed, then stop the scheduler."""
+        with self.cv:
+            self.closing = True
+            self.cv.notify_all()
         self.sched.join()
-        for t in self.threads:
+        for t in self.workers:
             t.join()
 
     def close(self):
         self.drain()
         for h in self.handles:
-            h.close()
+            if h is not None:
+                h.close()
+
+    # -- scheduler ------------------------------------------------------------
+    def _pick(self):
+        """Index of the first queued request that fits (FCFS with backfill), or None."""
+        if not self.idle:
+            return None
+        for i, req in enumerate(self.queue):
+            if self.in_use + req.footprint() <= self.budget:
+                return i
+        return None
+
+    def _schedule(self):
+        with self.cv:
+            while True:
+                i = self._pick()
+                if i is not None:
+                    req = self.queue[i]
+                    del self.queue[i]
+                    slot = self.idle.popleft()
+                    self.in_use += req.footprint()
+                    req.t_admit = time.perf_counter()
+                    req.slot = slot
+                    inflight = self.nslots - len(self.idle)
+                    self.max_in_flight = max(self.max_in_flight, inflight)
+                    t = threading.Thread(target=self._run, args=(slot, req), daemon=True)
+                    self.workers.append(t)
+                    t.start()
+                    continue
+                if self.closing and not self.queue and len(self.idle) == self.nslots:
+                    return
+                self.cv.wait(timeout=0.05)
+
+    def _run(self, slot, req):
+        try:
+            req.status, req.evals, req.resid, req.stats = self.solve_fn(slot, req)
+        except Exception:  # keep the service alive; the request reports the failure
+            req.status = -999
+        finally:
+            req.t_done = time.perf_counter()
+            with self.cv:
+                self.in_use -= req.footprint()
+                self.idle.append(slot)
+                self.completed.append(req)
+                self.cv.notify_all()
+            req.done.set()
 
 
 def latency_stats(reqs):
     lat = np.array([r.t_done - r.t_arrive for r in reqs])
     return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "count": len(lat)}
+            "mean_s": float(lat.mean()), "count": int(len(lat))}
