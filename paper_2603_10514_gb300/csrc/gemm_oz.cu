@@ -6,15 +6,16 @@
 //
 // Slicing.  Every row m of the (stacked real) A is scaled by 2^-e_m so that its
 // entries lie in (-1, 1), every column c of V by 2^-f_c, and each scaled entry
-// is cut into S = 8 signed 7-bit digits: x = sum_i d_i 2^{-7i} + O(2^-56),
-// |d_i| <= 127.  Digits are exact in BF16.  Then
+// is cut into S = 8 signed digits by rounding to nearest: x = sum_i d_i 2^{-7i}
+// + O(2^-57), |d_1| <= 128, |d_i| <= 64 (i > 1).  Digits are exact in BF16.  Then
 //   (A V)[m, c] = 2^{e_m + f_c} sum_{t=2}^{9} 2^{-7t} L_t[m, c],
 //   L_t = sum_{i + j = t} A_i V_j        (pairs with i + j > 9 are dropped:
 //                                         their weight is below 2^-63),
 // 36 BF16 products per output.  Levels 2..5 carry the leading bits and must
 // be summed exactly: each is an integer whose partial sum over a K chunk of
-// 256 is bounded by 4 * 256 * 127^2 < 2^24, so the tensor core's FP32
-// accumulation is exact; after every chunk the epilogue adds them, shifted
+// 256 is bounded by 256 * (2 * 128 * 64 + 2 * 64 * 64) < 2^23 (level 5, the
+// largest), so every partial sum is an integer FP32 represents and the tensor
+// core's FP32 accumulation is exact; after every chunk the epilogue adds them, shifted
 // into place, into one int64 per output, which stays exact over the whole K.
 // Levels 6..9 weigh at most 2^-28 of level 2, so FP32 accumulation over the
 // whole K (relative rounding 2^-24) keeps their error below 2^-52 of the
@@ -301,15 +302,20 @@ __device__ __forceinline__ int exp_bound(double amax) {
   return e;
 }
 
+// Digits by rounding to nearest: d_1 in [-128, 128], d_i in [-64, 64] for i > 1 (the
+// remainder after a nearest rounding is at most half a unit), all exact in BF16.  The
+// slicing error is then at most 2^-57 of the row / column scale and unbiased, so it
+// accumulates like a random walk over K instead of growing linearly as truncation's
+// one-signed error does.
 __device__ __forceinline__ void write_digits(double x, int e, __nv_bfloat16* base, size_t idx,
                                              size_t plane) {
   double r = ldexp(x, -e);  // |r| < 1, exact
 #pragma unroll
   for (int i = 0; i < OZ_S; ++i) {
     const double s = r * 128.0;
-    const double d = trunc(s);
+    const double d = rint(s);
     r = s - d;
-    base[idx + (size_t)i * plane] = __double2bfloat16(d);  // |d| <= 127: exact
+    base[idx + (size_t)i * plane] = __double2bfloat16(d);
   }
 }
 

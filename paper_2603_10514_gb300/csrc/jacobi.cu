@@ -4,12 +4,12 @@
 // Round-robin ordering: in each round the indices 0..L-1 (L = l rounded up to
 // even; index l is a dummy when l is odd) form L/2 disjoint pairs, so all L/2
 // rotations of a round commute and are applied together.  L - 1 rounds make a
-// sweep that visits every pair once.  One launch per round, H ping-ponged
-// between two buffers: each thread derives from H_in the rotations of its pairs
-// (pair (p, q), g = H_pq = |g| e^{i phi}, tau = (H_qq - H_pp) / (2|g|),
-// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c,
-// J = [[c, s e^{i phi}], [-s e^{-i phi}, c]]) and writes its 2x2 block of
-// J^H H_in J to H_out; W <- W J, one thread per (row, pair).
+// sweep that visits every pair once.  Per round:
+//   1. rot kernel: for pair (p, q) with g = H_pq = |g| e^{i phi},
+//        tau = (H_qq - H_pp) / (2|g|), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
+//        c = 1/sqrt(1 + t^2), s = t c,  J = [[c, s e^{i phi}], [-s e^{-i phi}, c]];
+//   2. apply kernel: H <- J^H H J, one thread per 2x2 block (pair_a, pair_b),
+//      and W <- W J, one thread per (row, pair).
 // Sweeps stop when the off-diagonal Frobenius norm is <= l 2^-53 ||H||_F (the
 // rounding level a parallel sweep leaves behind; eigenvalues are then accurate
 // to that level by Weyl's inequality) or after max_sweeps.
@@ -39,12 +39,10 @@ __device__ inline void pair_of(int L, int round, int i, int& p, int& q) {
   if (p > q) { int t = p; p = q; q = t; }
 }
 
-template <class T> __device__ inline T rot_s(const Rot& r);
-template <> __device__ inline double rot_s<double>(const Rot& r) { return r.sx; }
-template <> __device__ inline z64 rot_s<z64>(const Rot& r) { return z64{r.sx, r.sy}; }
-
 template <class T>
-__device__ inline Rot make_rot(int l, int L, int round, int i, const T* H, int ldh) {
+__global__ void jacobi_rot_kernel(int l, int L, int round, const T* H, int ldh, Rot* rots) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L / 2) return;
   int p, q;
   pair_of(L, round, i, p, q);
   Rot r;
@@ -68,15 +66,17 @@ __device__ inline Rot make_rot(int l, int L, int round, int i, const T* H, int l
       }
     }
   }
-  return r;
+  rots[i] = r;
 }
 
-// One whole round in one launch: every thread derives the rotations it needs from
-// Hin (unchanged during the launch) and writes its 2x2 block of J^H Hin J into Hout;
-// W <- W J in place (each (row, pair) element pair has one owner).
+template <class T> __device__ inline T rot_s(const Rot& r);
+template <> __device__ inline double rot_s<double>(const Rot& r) { return r.sx; }
+template <> __device__ inline z64 rot_s<z64>(const Rot& r) { return z64{r.sx, r.sy}; }
+
+// H <- J^H H J on the 2x2 block (rows of pair a, columns of pair b), and W <- W J.
 template <class T>
-__global__ void jacobi_round_kernel(int l, int L, int round, const T* __restrict__ Hin, int ldh,
-                                    T* __restrict__ Hout, T* W, int ldw) {
+__global__ void jacobi_apply_kernel(int l, int L, const Rot* __restrict__ rots, T* H, int ldh, T* W,
+                                    int ldw) {
   const int np = L / 2;
   const long long nblk = (long long)np * np;
   const long long nw = (long long)l * np;
@@ -84,40 +84,42 @@ __global__ void jacobi_round_kernel(int l, int L, int round, const T* __restrict
        t += (long long)gridDim.x * blockDim.x) {
     if (t < nblk) {
       const int a = (int)(t % np), b = (int)(t / np);
-      const Rot ra = make_rot<T>(l, L, round, a, Hin, ldh);
-      const Rot rb = (a == b) ? ra : make_rot<T>(l, L, round, b, Hin, ldh);
+      const Rot ra = rots[a], rb = rots[b];
       const int pa = ra.p, qa = ra.q, pb = rb.p, qb = rb.q;
       const bool va = qa < l, vb = qb < l;
-      T h_pp = Hin[(size_t)pa + (size_t)pb * ldh];
-      T h_qp = va ? Hin[(size_t)qa + (size_t)pb * ldh] : Sc<T>::zero();
-      T h_pq = vb ? Hin[(size_t)pa + (size_t)qb * ldh] : Sc<T>::zero();
-      T h_qq = (va && vb) ? Hin[(size_t)qa + (size_t)qb * ldh] : Sc<T>::zero();
+      // load the 2x2 block (dummy index -> zero row/column, never stored)
+      T h_pp = H[(size_t)pa + (size_t)pb * ldh];
+      T h_qp = va ? H[(size_t)qa + (size_t)pb * ldh] : Sc<T>::zero();
+      T h_pq = vb ? H[(size_t)pa + (size_t)qb * ldh] : Sc<T>::zero();
+      T h_qq = (va && vb) ? H[(size_t)qa + (size_t)qb * ldh] : Sc<T>::zero();
+      // right: [col p, col q] J_b = [c col_p - conj(s) col_q, s col_p + c col_q]
       const double cb = rb.c;
       const T sb = rot_s<T>(rb), sbc = Sc<T>::conj(sb);
       T r_pp = Sc<T>::sub(Sc<T>::scale(h_pp, cb), Sc<T>::mul(h_pq, sbc));
       T r_qp = Sc<T>::sub(Sc<T>::scale(h_qp, cb), Sc<T>::mul(h_qq, sbc));
       T r_pq = Sc<T>::add(Sc<T>::mul(h_pp, sb), Sc<T>::scale(h_pq, cb));
       T r_qq = Sc<T>::add(Sc<T>::mul(h_qp, sb), Sc<T>::scale(h_qq, cb));
+      // left: J_a^H [row p; row q] = [c row_p - s row_q; conj(s) row_p + c row_q]
       const double ca = ra.c;
       const T sa = rot_s<T>(ra), sac = Sc<T>::conj(sa);
       T o_pp = Sc<T>::sub(Sc<T>::scale(r_pp, ca), Sc<T>::mul(sa, r_qp));
       T o_pq = Sc<T>::sub(Sc<T>::scale(r_pq, ca), Sc<T>::mul(sa, r_qq));
       T o_qp = Sc<T>::add(Sc<T>::mul(sac, r_pp), Sc<T>::scale(r_qp, ca));
       T o_qq = Sc<T>::add(Sc<T>::mul(sac, r_pq), Sc<T>::scale(r_qq, ca));
-      if (a == b) {
+      if (a == b) {  // the rotated pair itself: exact zero off-diagonal, real diagonal
         o_pq = Sc<T>::zero();
         o_qp = Sc<T>::zero();
         o_pp = Sc<T>::from_re(Sc<T>::re(o_pp));
         o_qq = Sc<T>::from_re(Sc<T>::re(o_qq));
       }
-      Hout[(size_t)pa + (size_t)pb * ldh] = o_pp;
-      if (va) Hout[(size_t)qa + (size_t)pb * ldh] = o_qp;
-      if (vb) Hout[(size_t)pa + (size_t)qb * ldh] = o_pq;
-      if (va && vb) Hout[(size_t)qa + (size_t)qb * ldh] = o_qq;
+      H[(size_t)pa + (size_t)pb * ldh] = o_pp;
+      if (va) H[(size_t)qa + (size_t)pb * ldh] = o_qp;
+      if (vb) H[(size_t)pa + (size_t)qb * ldh] = o_pq;
+      if (va && vb) H[(size_t)qa + (size_t)qb * ldh] = o_qq;
     } else {
       const long long u = t - nblk;
       const int i = (int)(u % l), b = (int)(u / l);
-      const Rot rb = make_rot<T>(l, L, round, b, Hin, ldh);
+      const Rot rb = rots[b];
       if (rb.q >= l) continue;
       const double cb = rb.c;
       const T sb = rot_s<T>(rb), sbc = Sc<T>::conj(sb);
@@ -210,14 +212,13 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
   off_nrm = (off_nrm + 255) & ~(size_t)255;
   size_t off_perm = off_nrm + 256;
   size_t off_w = (off_perm + sizeof(int) * (size_t)l + 255) & ~(size_t)255;
-  size_t off_h2 = (off_w + sizeof(T) * (size_t)l * l + 255) & ~(size_t)255;
-  size_t need = off_h2 + sizeof(T) * (size_t)l * l;
+  size_t need = off_w + sizeof(T) * (size_t)l * l;
   if (need > work_bytes) return 4;  // CHASE_ERR_OOM
   char* base = (char*)work;
+  Rot* rots = (Rot*)(base + off_rot);
   double* dnrm = (double*)(base + off_nrm);
   int* dperm = (int*)(base + off_perm);
   T* Wtmp = (T*)(base + off_w);
-  T* H2 = (T*)(base + off_h2);  // ping-pong partner of H (leading dimension ldh)
   int nl = 0;
   int blocks = std::min(ceil_div((long long)l * l, 256), kNumSMs * 8);
   jacobi_init_kernel<T><<<blocks, 256, 0, st>>>(l, W, ldw);
@@ -227,10 +228,9 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
   if (l > 1) {
     const long long work_items = (long long)(L / 2) * (L / 2) + (long long)l * (L / 2);
     const int ablocks = std::min(ceil_div(work_items, 256), kNumSMs * 8);
-    T* Hc = H;   // current
-    T* Hn = H2;  // next
+    const int rblocks = ceil_div(L / 2, 128);
     for (sw = 0; sw < max_sweeps; ++sw) {
-      jacobi_offnorm_kernel<T><<<1, 1024, 0, st>>>(l, Hc, ldh, dnrm);
+      jacobi_offnorm_kernel<T><<<1, 1024, 0, st>>>(l, H, ldh, dnrm);
       ++nl;
       CHASE_CUDA_TRY(cudaMemcpyAsync(host_nrm, dnrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
       CHASE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -238,14 +238,11 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
       const double tolr = 1.1102230246251565e-16 * (double)l;
       if (host_nrm[0] <= tolr * tolr * host_nrm[1] || host_nrm[0] == 0.0) break;
       for (int r = 0; r < L - 1; ++r) {
-        jacobi_round_kernel<T><<<ablocks, 256, 0, st>>>(l, L, r, Hc, ldh, Hn, W, ldw);
-        ++nl;
-        T* tmp = Hc; Hc = Hn; Hn = tmp;
+        jacobi_rot_kernel<T><<<rblocks, 128, 0, st>>>(l, L, r, H, ldh, rots);
+        jacobi_apply_kernel<T><<<ablocks, 256, 0, st>>>(l, L, rots, H, ldh, W, ldw);
+        nl += 2;
       }
     }
-    if (Hc != H)
-      CHASE_CUDA_TRY(cudaMemcpy2DAsync(H, sizeof(T) * (size_t)ldh, Hc, sizeof(T) * (size_t)ldh,
-                                       sizeof(T) * (size_t)l, l, cudaMemcpyDeviceToDevice, st));
   }
   jacobi_sort_kernel<T><<<1, 1024, 0, st>>>(l, H, ldh, W, ldw, dw, dperm);
   ++nl;
