@@ -182,6 +182,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_aggregate(local_seconds, steps, world, dist=None, device=None):
+    """Replicas only: every rank solves its own problem.  The job's time is the slowest
+    rank's (max over ranks); the job's throughput counts every rank's solves."""
+    total = float(local_seconds)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total], dtype=torch.float64,
+                         device=device if device is not None else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return total, world * steps / total
+
+
 def make_problem(args, device):
     import workloads as W
     prob = W.c2_complex_clustered(n=args.n, nev=args.nev, nex=args.nex, seed=2)
@@ -439,17 +452,13 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     step_s = [evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(args.steps)]
-    total = evs[0].elapsed_time(evs[-1]) / 1e3
-    if dist:
-        t = torch.tensor([total], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total, value = replica_aggregate(evs[0].elapsed_time(evs[-1]) / 1e3, args.steps, world, dist,
+                                     device)
     # correctness of every timed solve
     lam = prob.lam[:prob.nev]
     ok = all(r[0] == 0 and float(r[2].max()) < prob.tol for r in results)
     eval_err = max(float(np.abs(r[1] - lam).max()) for r in results)
     rc, ev, res, st, logs = results[-1]
-    value = world * args.steps / total
     launches = sum(r[3]["kernel_launches"] for r in results)
     # roofline of the dominant kernel: the filter product (CUDA-event time of the filter phase,
     # which is almost all product launches, divided by the launch count)
@@ -520,11 +529,7 @@ def main():
             rc2, ev2, res2, st2, _ = P.chase_solve(h, A_d, V_d, prob.nev, prob.nex, bounds, cfg)
             Y_h.copy_(V_d[:, :prob.nev], non_blocking=True)
             torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([t_e2e], device=device, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e, _ = replica_aggregate(time.perf_counter() - t0, args.steps, world, dist, device)
         h2d = A_h.numel() * A_h.element_size() + V0_h.numel() * V0_h.element_size()
         d2h = Y_h.numel() * Y_h.element_size() + 2 * 8 * prob.nev
         line["e2e"] = {"value": world * args.steps / t_e2e, "unit": "solves/s",

@@ -139,7 +139,10 @@ int chase_reserve_workspace(chase_handle h, size_t bytes);
  * chase_solve -- Algorithm 1.
  *   n         matrix order (>= 1);  dA: n x n device matrix, lda >= n.
  *   nev, nex  wanted pairs and extra search vectors; ell = nev + nex <= n.
- *   cfg       options (NULL: defaults);  bounds: spectral estimates (required).
+ *   cfg       options (NULL: defaults).
+ *   bounds    spectral estimates, or NULL: then chase_lanczos_bounds runs first
+ *             with 4 runs (fewer if ell < 4) of min(25, n - 1) steps started at
+ *             the first columns of dV (the start block's random vectors).
  *   dV        device n x ell block, ldv >= n.  On entry: the start block V0 of
  *             Algorithm 1 (random or a warm start; need not be orthonormal).
  *             On exit: columns 0..nev-1 hold the eigenvectors Y in ascending
@@ -200,6 +203,25 @@ int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int 
  */
 int chase_cond_est(int ell, int nlocked, const double* ritz, const int* degrees, double lambda1,
                    double c, double e, double eta, double* est, double* log_est);
+
+/*
+ * chase_lanczos_bounds -- the spectral estimates Algorithm 1 takes before its
+ * loop ("estimate lambda_1, lambda_ell and lambda_n" by a few Lanczos runs).
+ *   nruns     runs, started at the columns of dV0 (device, n x nruns, ldv >= n;
+ *             random vectors supplied by the caller); steps: Lanczos steps per
+ *             run (1 <= steps < n), with full re-orthogonalisation.
+ *   ell       nev + nex, the index whose eigenvalue lambda_ell estimates.
+ *   out       host: lambda1 = smallest Ritz value of all runs; b_sup = largest
+ *             (Ritz value + |last beta|) of a run, an upper bound of lambda_n;
+ *             lambda_ell = the smallest Ritz value at which the spectral-density
+ *             estimate (n / nruns) sum_runs sum_{theta_i <= x} tau_i reaches ell
+ *             (tau_i: squared first component of the tridiagonal's eigenvector).
+ * The reading of how the three numbers are formed is this library's (the paper
+ * names the Lanczos step without its formulas).
+ */
+int chase_lanczos_bounds(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda,
+                         int nruns, const void* dV0, int ldv, int steps, int ell,
+                         chase_bounds* out);
 
 /* Static description of a status code. */
 const char* chase_status_string(int status);

@@ -84,6 +84,7 @@ def lib():
             _lib.orc_qr_dynamic.argtypes = [i, i, P, i, d, d, d, i, P]
             _lib.orc_jacobi_eig.argtypes = [i, P, i, P, P, i]
             _lib.orc_jacobi_svd.argtypes = [i, i, P, i, P]
+            _lib.orc_lanczos_bounds.argtypes = [i, P, i, i, P, i, i, i, P, P]
             _lib.orc_solve.argtypes = [i, P, i, i, i, P, i, ctypes.POINTER(Params), P, P, P,
                                        ctypes.POINTER(Summary)]
         return _lib
@@ -196,6 +197,17 @@ def jacobi_svd(X):
     sv = np.zeros(X_.shape[1])
     lib().orc_jacobi_svd(X_.shape[0], X_.shape[1], _ptr(X_), X_.shape[0], _ptr(sv))
     return sv
+
+
+def lanczos_bounds(A, V0, steps, ell):
+    """(lambda1, lambda_ell, b_sup) estimates from Lanczos runs started at the columns of V0,
+    plus every run's Ritz values (nruns x steps)."""
+    A_, V_ = _c128(A), _c128(V0)
+    n, r = V_.shape
+    out = np.zeros(3)
+    ritz = np.zeros((r, steps))
+    lib().orc_lanczos_bounds(n, _ptr(A_), n, r, _ptr(V_), n, steps, ell, _ptr(out), _ptr(ritz))
+    return tuple(out), ritz
 
 
 def solve(A, V0, nev, nex, *, tol=1e-10, max_iter=25, deg_init=20, deg_min=10, deg_max=36,

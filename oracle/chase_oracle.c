@@ -472,6 +472,97 @@ int orc_jacobi_svd(int n, int l, const cplx* X, int ldx, double* sv) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Spectral bounds by a few Lanczos runs (Algorithm 1, "estimate lambda_1,   */
+/* lambda_ell and lambda_n")                                                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * nruns Lanczos runs of m steps from the columns of V0 (n x nruns), with full
+ * re-orthogonalisation against the run's basis.  Each run yields the tridiagonal
+ * T = tridiag(beta, alpha, beta), its eigenvalues theta_i (Ritz values) and the
+ * squared first components tau_i of its eigenvectors.  Reading of the paper's
+ * one-line description:
+ *   b_sup       = max over runs of (theta_max + |beta_m|)     (an upper bound of lambda_n)
+ *   lambda1     = min over runs of theta_min
+ *   lambda_ell  = the smallest pooled Ritz value at which the spectral-density
+ *                 estimate  (n / nruns) sum_runs sum_{theta_i <= x} tau_i  reaches ell.
+ * Outputs the three numbers in out[0..2] and every run's Ritz values in ritz
+ * (nruns x m, may be NULL).
+ */
+int orc_lanczos_bounds(int n, const cplx* A, int lda, int nruns, const cplx* V0, int ldv, int m,
+                       int ell, double* out, double* ritz_out) {
+  cplx* Q = malloc(sizeof(cplx) * (size_t)n * (m + 1));
+  cplx* w = malloc(sizeof(cplx) * (size_t)n);
+  double* alpha = malloc(sizeof(double) * m);
+  double* beta = malloc(sizeof(double) * m);
+  cplx* T = malloc(sizeof(cplx) * (size_t)m * m);
+  cplx* S = malloc(sizeof(cplx) * (size_t)m * m);
+  double* th = malloc(sizeof(double) * (size_t)nruns * m);
+  double* tau = malloc(sizeof(double) * (size_t)nruns * m);
+  double bsup = -1e300, l1 = 1e300;
+  for (int r = 0; r < nruns; ++r) {
+    const cplx* v = V0 + IDX(0, r, ldv);
+    double nv = orc_nrm2(n, v);
+    for (int i = 0; i < n; ++i) Q[i] = v[i] / nv;
+    for (int j = 0; j < m; ++j) {
+      cplx* q = Q + IDX(0, j, n);
+      orc_matmul_block(n, A, lda, 1, q, n, w, n);
+      cplx a = 0;
+      for (int i = 0; i < n; ++i) a += conj(q[i]) * w[i];
+      alpha[j] = creal(a);
+      for (int i = 0; i < n; ++i) w[i] -= alpha[j] * q[i];
+      if (j > 0)
+        for (int i = 0; i < n; ++i) w[i] -= beta[j - 1] * Q[IDX(i, j - 1, n)];
+      /* full re-orthogonalisation (classical Gram-Schmidt, once) */
+      for (int p = 0; p <= j; ++p) {
+        cplx d = 0;
+        for (int i = 0; i < n; ++i) d += conj(Q[IDX(i, p, n)]) * w[i];
+        for (int i = 0; i < n; ++i) w[i] -= d * Q[IDX(i, p, n)];
+      }
+      beta[j] = orc_nrm2(n, w);
+      cplx* qn = Q + IDX(0, j + 1, n);
+      for (int i = 0; i < n; ++i) qn[i] = (beta[j] > 0.0) ? w[i] / beta[j] : 0.0;
+    }
+    for (int p = 0; p < m; ++p)
+      for (int q = 0; q < m; ++q) T[IDX(p, q, m)] = 0;
+    for (int p = 0; p < m; ++p) {
+      T[IDX(p, p, m)] = alpha[p];
+      if (p + 1 < m) { T[IDX(p, p + 1, m)] = beta[p]; T[IDX(p + 1, p, m)] = beta[p]; }
+    }
+    double* thr = th + (size_t)r * m;
+    orc_jacobi_eig(m, T, m, thr, S, m);
+    for (int i = 0; i < m; ++i) {
+      double s0 = cabs(S[IDX(0, i, m)]);
+      tau[(size_t)r * m + i] = s0 * s0;
+    }
+    if (thr[m - 1] + fabs(beta[m - 1]) > bsup) bsup = thr[m - 1] + fabs(beta[m - 1]);
+    if (thr[0] < l1) l1 = thr[0];
+    if (ritz_out)
+      for (int i = 0; i < m; ++i) ritz_out[(size_t)r * m + i] = thr[i];
+  }
+  /* spectral-density estimate: pooled Ritz values in ascending order */
+  const int tot = nruns * m;
+  int* ord = malloc(sizeof(int) * tot);
+  for (int i = 0; i < tot; ++i) ord[i] = i;
+  for (int i = 1; i < tot; ++i) { /* insertion sort by theta, ties by index */
+    int k = ord[i], j = i - 1;
+    while (j >= 0 && th[ord[j]] > th[k]) { ord[j + 1] = ord[j]; --j; }
+    ord[j + 1] = k;
+  }
+  double cum = 0.0, lell = th[ord[tot - 1]];
+  for (int i = 0; i < tot; ++i) {
+    cum += tau[ord[i]] * (double)n / (double)nruns;
+    if (cum >= (double)ell) { lell = th[ord[i]]; break; }
+  }
+  if (lell < l1) lell = l1;
+  out[0] = l1;
+  out[1] = lell;
+  out[2] = bsup;
+  free(ord); free(Q); free(w); free(alpha); free(beta); free(T); free(S); free(th); free(tau);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The ChASE outer loop (Algorithm 1)                                        */
 /* ------------------------------------------------------------------------ */
 

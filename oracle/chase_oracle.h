@@ -49,6 +49,8 @@ int orc_qr_dynamic(int n, int l, double complex* X, int ldx, double log_est, dou
                    double cond_lo, int force, int* chol_fail_info);
 int orc_jacobi_eig(int l, double complex* H, int ldh, double* w, double complex* W, int ldw);
 int orc_jacobi_svd(int n, int l, const double complex* X, int ldx, double* sv);
+int orc_lanczos_bounds(int n, const double complex* A, int lda, int nruns, const double complex* V0,
+                       int ldv, int m, int ell, double* out, double* ritz_out);
 int orc_solve(int n, const double complex* A, int lda, int nev, int nex, double complex* V, int ldv,
               const orc_params* prm, double* evals, double* resid, orc_iter_log* logs,
               orc_summary* sum);

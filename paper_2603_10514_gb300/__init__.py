@@ -29,7 +29,7 @@ QR_VARIANTS = {1: "cholqr1", 2: "cholqr2", 3: "shifted_cholqr2", 4: "householder
 
 EXPORTED = ["chase_create", "chase_destroy", "chase_config_default", "chase_workspace_bytes",
             "chase_solve", "chase_filter", "chase_qr", "chase_cond_est", "chase_status_string",
-            "chase_filter_noalloc", "chase_reserve_workspace"]
+            "chase_filter_noalloc", "chase_reserve_workspace", "chase_lanczos_bounds"]
 
 
 class ChaseError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
         L.chase_config_default.argtypes = [ctypes.POINTER(Config)]
         L.chase_workspace_bytes.argtypes = [i, i, i, i, i, ctypes.POINTER(ctypes.c_size_t)]
         L.chase_reserve_workspace.argtypes = [P, ctypes.c_size_t]
+        L.chase_lanczos_bounds.argtypes = [P, i, i, P, i, i, P, i, i, i, ctypes.POINTER(Bounds)]
         L.chase_solve.argtypes = [P, i, i, P, i, i, i, ctypes.POINTER(Config), ctypes.POINTER(Bounds),
                                   P, i, P, P, ctypes.POINTER(Stats), P, i]
         L.chase_filter.argtypes = [P, i, i, P, i, i, P, i, P, d, d, d, i, P, i]
@@ -191,13 +192,13 @@ def chase_solve(h, A, V, nev, nex, bounds, cfg=None, log_cap=64, check=True):
     lda, ldv = _ld(A, "A"), _ld(V, "V")
     if cfg is None:
         cfg = config_default()
-    b = Bounds(*[float(x) for x in bounds])
+    b = Bounds(*[float(x) for x in bounds]) if bounds is not None else None
     evals = np.zeros(nev)
     resid = np.zeros(nev)
     st = Stats()
     logs = (IterLog * max(1, log_cap))()
     rc = lib().chase_solve(h.ptr, dt, n, ctypes.c_void_p(A.data_ptr()), lda, nev, nex, ctypes.byref(cfg),
-                           ctypes.byref(b), ctypes.c_void_p(V.data_ptr()), ldv,
+                           ctypes.byref(b) if b is not None else None, ctypes.c_void_p(V.data_ptr()), ldv,
                            evals.ctypes.data_as(ctypes.c_void_p), resid.ctypes.data_as(ctypes.c_void_p),
                            ctypes.byref(st), ctypes.cast(logs, ctypes.c_void_p), log_cap)
     if check and rc not in (CHASE_OK, CHASE_NOT_CONVERGED):
@@ -237,6 +238,20 @@ def chase_qr(h, X, est_cond, qr_force=0, check=True):
     if check and rc not in (CHASE_OK, CHASE_CHOL_FAILED):
         raise ChaseError(rc, "chase_qr")
     return rc, v.value, info.value
+
+
+def chase_lanczos_bounds(h, A, V0, steps, ell):
+    """(lambda1, lambda_ell, b_sup) from Lanczos runs started at the columns of V0 (CUDA)."""
+    n = A.shape[0]
+    dt = _dtype_code(A)
+    lda, ldv = _ld(A, "A"), _ld(V0, "V0")
+    out = Bounds()
+    rc = lib().chase_lanczos_bounds(h.ptr, dt, n, ctypes.c_void_p(A.data_ptr()), lda, V0.shape[1],
+                                    ctypes.c_void_p(V0.data_ptr()), ldv, int(steps), int(ell),
+                                    ctypes.byref(out))
+    if rc:
+        raise ChaseError(rc, "chase_lanczos_bounds")
+    return out.lambda1, out.lambda_ell, out.b_sup
 
 
 def chase_cond_est(ritz, degrees, nlocked, lambda1, c, e, eta=1.0):

@@ -107,4 +107,12 @@ int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowe
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
             DevStatus* dst, int* launches);
 
+// ---- Lanczos spectral bounds (lanczos.cu) ----------------------------------
+// out = {lambda1, lambda_ell, b_sup} from nruns runs of m steps started at V0's columns.
+template <class T>
+int lanczos_bounds(cudaStream_t st, int n, const T* A, int lda, int nruns, const T* V0, int ldv,
+                   int m, int ell, double* out, void* work, size_t work_bytes, Scratch scr,
+                   int* launches);
+size_t lanczos_work_bytes(size_t elem, int n, int nruns, int m);
+
 }  // namespace chase

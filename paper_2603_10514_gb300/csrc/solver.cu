@@ -765,6 +765,27 @@ int qr_impl(chase_ctx* h, int n, int l, T* X, int ldx, double est, int force, in
   return rc;
 }
 
+int lanczos_entry(chase_ctx* h, chase_dtype dtype, int n, const void* dA, int lda, int nruns,
+                  const void* dV0, int ldv, int steps, int ell, chase_bounds* out) {
+  const size_t elem = (dtype == CHASE_R64) ? sizeof(double) : sizeof(z64);
+  const size_t wb = lanczos_work_bytes(elem, n, nruns, steps);
+  TRY(ensure_ws(h, wb + kScratchBytes));
+  Scratch scr{(char*)h->ws + wb, kScratchBytes};
+  double b[3];
+  int rc;
+  if (dtype == CHASE_R64)
+    rc = lanczos_bounds<double>(h->stream, n, (const double*)dA, lda, nruns, (const double*)dV0, ldv,
+                                steps, ell, b, h->ws, wb, scr, &h->launches);
+  else
+    rc = lanczos_bounds<z64>(h->stream, n, (const z64*)dA, lda, nruns, (const z64*)dV0, ldv, steps,
+                             ell, b, h->ws, wb, scr, &h->launches);
+  if (rc) return rc;
+  out->lambda1 = b[0];
+  out->lambda_ell = b[1];
+  out->b_sup = b[2];
+  return CHASE_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -871,7 +892,7 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
   if (c.prec != CHASE_FP64 && c.prec != CHASE_BF16X3 && c.prec != CHASE_FP64_EMU)
     return CHASE_ERR_UNSUPPORTED;
   if (c.prec == CHASE_BF16X3 && !(c.mp_switch >= 0.0)) return -8;
-  if (!bounds || !(bounds->b_sup > bounds->lambda_ell) || !(bounds->lambda_ell >= bounds->lambda1))
+  if (bounds && (!(bounds->b_sup > bounds->lambda_ell) || !(bounds->lambda_ell >= bounds->lambda1)))
     return -9;
   if (!dV) return -10;
   if (ldv < n) return -11;
@@ -879,10 +900,21 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
   if (!resid) return -13;
   if (log_cap < 0) return -16;
   if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  chase_bounds bd;
+  if (bounds) {
+    bd = *bounds;
+  } else {
+    if (n < 3) return -9;
+    const int l = nev + nex;
+    const int nruns = std::min(4, l), steps = std::min(25, n - 1);
+    int rc = lanczos_entry(h, dtype, n, dA, lda, nruns, dV, ldv, steps, l, &bd);
+    if (rc) return rc;
+    if (!(bd.b_sup > bd.lambda_ell)) bd.lambda_ell = 0.5 * (bd.lambda1 + bd.b_sup);
+  }
   if (dtype == CHASE_R64)
-    return solve_impl<double>(h, n, (const double*)dA, lda, nev, nex, c, *bounds, (double*)dV, ldv,
+    return solve_impl<double>(h, n, (const double*)dA, lda, nev, nex, c, bd, (double*)dV, ldv,
                               evals, resid, stats, log, log_cap);
-  return solve_impl<z64>(h, n, (const z64*)dA, lda, nev, nex, c, *bounds, (z64*)dV, ldv, evals,
+  return solve_impl<z64>(h, n, (const z64*)dA, lda, nev, nex, c, bd, (z64*)dV, ldv, evals,
                          resid, stats, log, log_cap);
 }
 
@@ -929,6 +961,24 @@ int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int 
   if (dtype == CHASE_R64)
     return qr_impl<double>(h, n, ncols, (double*)dX, ldx, est_cond, qr_force, variant_used, chol_info);
   return qr_impl<z64>(h, n, ncols, (z64*)dX, ldx, est_cond, qr_force, variant_used, chol_info);
+}
+
+int chase_lanczos_bounds(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda,
+                         int nruns, const void* dV0, int ldv, int steps, int ell,
+                         chase_bounds* out) {
+  if (!h) return -1;
+  if (dtype != CHASE_R64 && dtype != CHASE_C128) return -2;
+  if (n < 2) return -3;
+  if (!dA) return -4;
+  if (lda < n) return -5;
+  if (nruns < 1 || nruns > 32) return -6;
+  if (!dV0) return -7;
+  if (ldv < n) return -8;
+  if (steps < 1 || steps >= n || steps > 256) return -9;
+  if (ell < 1 || ell > n) return -10;
+  if (!out) return -11;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  return lanczos_entry(h, dtype, n, dA, lda, nruns, dV0, ldv, steps, ell, out);
 }
 
 int chase_cond_est(int ell, int nlocked, const double* ritz, const int* degrees, double lambda1,

@@ -273,3 +273,28 @@ def test_qr_blocked_cholesky_paths(cl, handle, complex_, l, log10k):
         assert np.abs(Q - Qo).max() <= 1e-8
     R = Q.conj().T @ X
     assert np.linalg.norm(np.tril(R, -1)) <= 1e-10 * np.linalg.norm(X)
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_lanczos_bounds_match_oracle(cl, handle, complex_):
+    n, ell = 700, 40
+    lam = W.spectrum_clustered(n, 60, 3) if complex_ else W.spectrum_uniform(n, -1, 1, 3)
+    A_t = W.known_spectrum_matrix(lam, 3, complex_, device="cuda")
+    V = W.start_block(n, 4, 77, complex_)
+    ref, _ = oracle.lanczos_bounds(host(A_t), V, 25, ell)
+    got = cl.chase_lanczos_bounds(handle, A_t, dev(V), 25, ell)
+    scale = lam[-1] - lam[0]
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-9 * scale)
+    assert got[2] >= lam[-1] and got[0] >= lam[0] - 1e-12
+
+
+def test_solve_without_bounds_runs_lanczos(cl, handle):
+    """bounds = NULL: the solve estimates them by Lanczos from its start block and still
+    reaches the known spectrum."""
+    prob = W.c2_complex_clustered(n=900, nev=30, nex=10, seed=21)
+    A_t = W.known_spectrum_matrix(prob.lam, prob.seed, True, device="cuda")
+    V0 = dev(W.start_block(prob.n, prob.ell, prob.seed, True))
+    rc, ev, res, st, _ = cl.chase_solve(handle, A_t, V0, prob.nev, prob.nex, None,
+                                        cl.config_default(opt_degree=1, prec=cl.CHASE_FP64_EMU))
+    assert rc == 0 and res.max() < prob.tol
+    assert np.abs(ev - prob.lam[:prob.nev]).max() <= 1e-10 * np.abs(prob.lam).max()

@@ -477,3 +477,43 @@ def test_estimate_bounds_exact_kappa_in_solve_first_iteration():
     sv = oracle.jacobi_svd(Vf)
     est = math.exp(oracle.log_cond_est(l1, prob.deg_init, prob.deg_init, l1, c, e, 1.0))
     assert sv[0] / sv[-1] <= est
+
+
+# --------------------------------------------------------------------------
+# Lanczos spectral bounds (Algorithm 1's estimation step)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_lanczos_bounds_bracket_the_spectrum(complex_):
+    """Ritz values lie inside [lambda_1, lambda_n] (Cauchy interlacing), so the lambda1
+    estimate is >= lambda_1; b_sup = theta_max + |beta_m| is >= lambda_n; both are close
+    after 25 steps on spectra with well-separated ends."""
+    for seed, spec in [(3, W.spectrum_uniform(300, -1, 1, 3)), (4, W.spectrum_clustered(300, 40, 4))]:
+        A = W.known_spectrum_matrix(spec, seed, complex_).numpy()
+        V = W.start_block(300, 4, seed + 50, complex_)
+        (l1, lell, bsup), ritz = oracle.lanczos_bounds(A, V, 25, 30)
+        assert l1 >= spec[0] - 1e-12 and l1 - spec[0] < 0.05 * (spec[-1] - spec[0])
+        assert bsup >= spec[-1]
+        assert ritz.min() >= spec[0] - 1e-12 and ritz.max() <= spec[-1] + 1e-12
+        assert l1 <= lell <= bsup
+
+
+def test_lanczos_full_length_reproduces_the_spectrum():
+    """n steps with full re-orthogonalisation on a tiny matrix span the whole space: the
+    Ritz values of each run are the eigenvalues (brute force against eigvalsh), the last
+    beta vanishes, and the spectral-density estimate counts all n eigenvalues (the weights
+    of a run sum to one)."""
+    n = 12
+    G = W.gaussian((n, n), 8, True)
+    A = 0.5 * (G + G.conj().T)
+    lam = np.linalg.eigvalsh(A)
+    V = W.start_block(n, 2, 9, True)
+    (l1, lell, bsup), ritz = oracle.lanczos_bounds(A, V, n, n)
+    for r in range(2):
+        np.testing.assert_allclose(np.sort(ritz[r]), lam, atol=1e-9)
+    assert abs(l1 - lam[0]) < 1e-9
+    assert abs(bsup - lam[-1]) < 1e-8
+    assert abs(lell - lam[-1]) < 1e-9
+    # fewer steps: interlacing Ritz values inside the spectrum
+    (_, _, _), ritz = oracle.lanczos_bounds(A, V, n - 1, n)
+    assert ritz.min() >= lam[0] - 1e-12 and ritz.max() <= lam[-1] + 1e-12
