@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=8)
-    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "sequence", "serve"],
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "filter", "sequence", "serve", "kappa"],
                     help="solve: the headline time-to-solution; filter: chase_filter alone "
                          "(kernel-level timing and small cases for profilers); sequence: 20 "
                          "correlated real problems with warm starts; serve: a stream of "
@@ -218,6 +219,73 @@ def oracle_sample(A_host, prob, cols, deg=2):
     oracle.filter(A_host, V, [deg] * cols, c, e, l1)
     dt = time.perf_counter() - t0
     return dt / (cols * deg), dt
+
+
+def device_view(ptr, n, ncols, ld, complex_):
+    """A torch view (no copy) of a column-major device block given by its raw pointer,
+    through the CUDA array interface."""
+    import torch
+
+    class _Block:
+        __cuda_array_interface__ = {
+            "shape": (ncols, ld), "typestr": "<c16" if complex_ else "<f8",
+            "data": (int(ptr), False), "version": 3, "strides": None}
+
+    return torch.as_tensor(_Block(), device="cuda").mT[:n, :]
+
+
+def run_kappa(args):
+    """Figure 2 analogue: per iteration, the estimate of Eq. full-est (kappa_est, logged by
+    the solver) against the exact kappa_2 of the block [Y V] Algorithm 3 factors (singular
+    values of a host copy, taken through the solver's filtered-block hook), with degree
+    optimisation (first degree 20, cap 36) and without it (degree 20)."""
+    import numpy as np
+    import torch
+
+    import paper_2603_10514_gb300 as P
+    import workloads as W
+    P.build()
+    n = args.n if args.n != 10000 else 3000
+    nev = args.nev if args.nev != 500 else 150
+    nex = args.nex if args.nex != 100 else 30
+    out = {"mode": "kappa", "prec": args.prec, "n": n, "nev": nev, "nex": nex, "runs": []}
+    for name, prob in [("complex clustered", W.c2_complex_clustered(n=n, nev=nev, nex=nex, seed=2)),
+                       ("real uniform", W.Problem("real", n, nev, nex, False, 1,
+                                                  W.spectrum_uniform(n, -1, 1, 1)))]:
+        A = W.known_spectrum_matrix(prob.lam, prob.seed, prob.complex_, device="cuda")
+        V0 = W.start_block(n, prob.ell, prob.seed, prob.complex_)
+        for opt in (False, True):
+            kap = {}
+
+            def hook(ptr, nn, ll, ld, it):
+                X = device_view(ptr, nn, ll, ld, prob.complex_).cpu().numpy()
+                sv = np.linalg.svd(X, compute_uv=False)
+                kap[it] = float(sv[0] / sv[-1])
+
+            h = P.Handle(0)
+            cfg = P.config_default(opt_degree=int(opt), deg_init=20, deg_max=36,
+                                   prec=PRECS[args.prec](P))
+            keep = P.with_filtered_hook(cfg, hook)
+            Vd = torch.from_numpy(np.ascontiguousarray(V0.T)).cuda().mT
+            rc, ev, res, st, logs = P.chase_solve(h, A, Vd, nev, nex, prob.bounds, cfg)
+            h.close()
+            del keep
+            rows = [{"it": g["iteration"], "locked": g["locked_before"], "variant": g["variant"],
+                     "log10_kappa_est": g["log_cond_est_paper"] / np.log(10.0),
+                     "log10_kappa_est_locked_aware": g["log_cond_est_locked"] / np.log(10.0),
+                     "log10_kappa_exact": float(np.log10(kap[g["iteration"]]))} for g in logs]
+            out["runs"].append({"problem": name, "opt": opt, "status": rc,
+                                "iterations": st["iterations"], "matvecs": st["matvecs"],
+                                "estimate_bounds_exact_before_locking":
+                                    all(r["log10_kappa_est"] >= r["log10_kappa_exact"]
+                                        for r in rows if r["locked"] == 0),
+                                "estimate_bounds_exact_in_all_iterations":
+                                    all(r["log10_kappa_est"] >= r["log10_kappa_exact"] for r in rows),
+                                "locked_aware_bounds_exact_in_all_iterations":
+                                    all(r["log10_kappa_est_locked_aware"] >= r["log10_kappa_exact"]
+                                        for r in rows),
+                                "per_iteration": rows})
+    print(json.dumps(out), flush=True)
 
 
 def run_sequence(args):
@@ -401,6 +469,9 @@ def main():
         return
     if args.mode == "sequence":
         run_sequence(args)
+        return
+    if args.mode == "kappa":
+        run_kappa(args)
         return
     if args.mode == "serve":
         run_serve(args)

@@ -84,7 +84,19 @@ typedef struct {
   double mp_switch;  /* mixed mode: the filter runs in BF16x3 until the largest residual of the
                         unlocked wanted pairs drops to mp_switch * max(|lambda1|, |b_sup|),
                         then in FP64 for the remaining iterations (default 1e-3) */
-  int reserved[6];
+  /* Observability (the per-iteration data of Figure 2): if set, called after
+   * every filter, before the QR, with the device block [Y V] that Algorithm 3
+   * is about to factor (n x ell, ld n, the solve's dtype) and the iteration
+   * number (1-based).  The block must not be modified; the call is synchronous
+   * with the solve's stream.  NULL (default): no call. */
+  void (*filtered_hook)(void* ctx, const void* dX, int n, int ell, int ldx, int iteration);
+  void* filtered_hook_ctx;
+  /* 0 (default): the estimate of Eq. full-est as printed.  1: the larger of it and
+   * eta |rho_1|^{m_ell}.  Once pairs are locked, [Y V] has the unit singular values
+   * of Y while the filter's gains are <= 1, so kappa_2([Y V]) can exceed Eq. full-est
+   * (measured: up to ~10x); |rho_1|^{m_ell} bounds 1 / (smallest gain). */
+  int cond_est_mode;
+  int reserved[5];
 } chase_config;
 
 /* Spectral information the filter needs (Algorithm 1, step "estimate lambda_1,
@@ -113,7 +125,8 @@ typedef struct {
 typedef struct {
   int iteration, locked_before, locked_after, variant, chol_fail_info, deg_min, deg_max;
   long long matvecs;
-  double log_cond_est, c, e, mu1, mu_ell;
+  double log_cond_est, c, e, mu1, mu_ell;     /* log_cond_est: the estimate that chose the QR */
+  double log_cond_est_paper, log_cond_est_locked; /* both forms (see cond_est_mode) */
 } chase_iter_log;
 
 /* Creates a handle bound to CUDA device `device`.  `cuda_stream` is a

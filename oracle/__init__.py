@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("deg_min", ctypes.c_int), ("deg_max", ctypes.c_int), ("opt_degree", ctypes.c_int),
                 ("eta", ctypes.c_double), ("cond_hi", ctypes.c_double), ("cond_lo", ctypes.c_double),
                 ("qr_force", ctypes.c_int), ("lambda1", ctypes.c_double),
-                ("lambda_ell", ctypes.c_double), ("b_sup", ctypes.c_double)]
+                ("lambda_ell", ctypes.c_double), ("b_sup", ctypes.c_double),
+                ("cond_est_mode", ctypes.c_int), ("log_exact_kappa", ctypes.c_int)]
 
 
 class IterLog(ctypes.Structure):
@@ -55,7 +56,9 @@ class IterLog(ctypes.Structure):
                 ("chol_fail_info", ctypes.c_int), ("deg_min", ctypes.c_int),
                 ("deg_max", ctypes.c_int), ("matvecs", ctypes.c_longlong),
                 ("log_cond_est", ctypes.c_double), ("c", ctypes.c_double), ("e", ctypes.c_double),
-                ("mu1", ctypes.c_double), ("mu_ell", ctypes.c_double)]
+                ("mu1", ctypes.c_double), ("mu_ell", ctypes.c_double),
+                ("log_cond_est_paper", ctypes.c_double), ("log_cond_est_locked", ctypes.c_double),
+                ("log_kappa_exact", ctypes.c_double)]
 
 
 class Summary(ctypes.Structure):
@@ -212,7 +215,7 @@ def lanczos_bounds(A, V0, steps, ell):
 
 def solve(A, V0, nev, nex, *, tol=1e-10, max_iter=25, deg_init=20, deg_min=10, deg_max=36,
           opt_degree=False, eta=1.0, cond_hi=1e8, cond_lo=20.0, qr_force=0, lambda1, lambda_ell,
-          b_sup):
+          b_sup, cond_est_mode=0, log_exact_kappa=False):
     """Algorithm 1.  Returns a dict with evals, resid, Y (n x nev), V (final block),
     per-iteration logs and the summary counters."""
     real = not np.iscomplexobj(A) and not np.iscomplexobj(V0)
@@ -221,7 +224,7 @@ def solve(A, V0, nev, nex, *, tol=1e-10, max_iter=25, deg_init=20, deg_min=10, d
     l = nev + nex
     assert V_.shape == (n, l)
     prm = Params(tol, max_iter, deg_init, deg_min, deg_max, int(opt_degree), eta, cond_hi, cond_lo,
-                 qr_force, lambda1, lambda_ell, b_sup)
+                 qr_force, lambda1, lambda_ell, b_sup, cond_est_mode, int(log_exact_kappa))
     evals = np.zeros(nev)
     resid = np.zeros(nev)
     logs = (IterLog * max(max_iter, 1))()

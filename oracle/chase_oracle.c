@@ -632,7 +632,20 @@ int orc_solve(int n, const cplx* A, int lda, int nev, int nex, cplx* V, int ldv,
     /* condition estimate (Eq. full-est); at the first iteration every column
      * still carries mu1 as its Ritz value, which gives Eq. simple-est */
     double theta_k1 = (it == 0) ? mu1 : ritz[k];
-    double lest = orc_log_cond_est(theta_k1, deg[k], deg[l - 1], mu1, c, e, prm->eta);
+    double lest_paper = orc_log_cond_est(theta_k1, deg[k], deg[l - 1], mu1, c, e, prm->eta);
+    /* the locked block Y contributes unit singular values: with filter gains <= 1 the
+     * largest singular value of [Y V] is 1, and the smallest is bounded below by the gain
+     * |rho_1|^{-m_ell} of the last column; the locked-aware form takes that bound too */
+    double lest_locked = log(prm->eta) + (double)deg[l - 1] * log(orc_abs_rho(mu1, c, e));
+    if (lest_locked < lest_paper) lest_locked = lest_paper;
+    double lest = (prm->cond_est_mode == 1) ? lest_locked : lest_paper;
+    double lkap = 0.0;
+    if (prm->log_exact_kappa) {
+      double* sv = malloc(sizeof(double) * l);
+      orc_jacobi_svd(n, l, V, ldv, sv);
+      lkap = log(sv[0] / sv[l - 1]);
+      free(sv);
+    }
     /* QR of [Y V] */
     for (int q = 0; q < k; ++q)
       for (int i = 0; i < n; ++i) Yk[IDX(i, q, n)] = V[IDX(i, q, ldv)];
@@ -681,6 +694,8 @@ int orc_solve(int n, const cplx* A, int lda, int nev, int nex, cplx* V, int ldv,
       g->iteration = it + 1; g->locked_before = k; g->locked_after = knew;
       g->log_cond_est = lest; g->variant = variant; g->chol_fail_info = fi;
       g->matvecs = matvecs; g->c = c; g->e = e; g->mu1 = mu1; g->mu_ell = mu_ell;
+      g->log_cond_est_paper = lest_paper; g->log_cond_est_locked = lest_locked;
+      g->log_kappa_exact = lkap;
       g->deg_min = deg[k]; g->deg_max = deg[l - 1];
     }
     /* spectral bounds for the next filter */

@@ -21,12 +21,16 @@ typedef struct {
   double lambda1;      /* estimate of the lowest eigenvalue */
   double lambda_ell;   /* estimate of the ell-th eigenvalue (lower edge of the damped interval) */
   double b_sup;        /* upper bound of the spectrum (must be >= lambda_n) */
+  int cond_est_mode;   /* 0: Eq. full-est as printed; 1: max(Eq. full-est, eta |rho_1|^{m_ell}) */
+  int log_exact_kappa; /* 1: log kappa_2 of [Y V] before each QR (one-sided Jacobi SVD) */
 } orc_params;
 
 typedef struct {
   int iteration, locked_before, locked_after, variant, chol_fail_info, deg_min, deg_max;
   long long matvecs;
   double log_cond_est, c, e, mu1, mu_ell;
+  double log_cond_est_paper, log_cond_est_locked; /* both forms, whichever drove the choice */
+  double log_kappa_exact;  /* ln kappa_2([Y V]) when requested, else 0 */
 } orc_iter_log;
 
 typedef struct {

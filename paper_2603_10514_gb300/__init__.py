@@ -43,7 +43,12 @@ class Config(ctypes.Structure):
                 ("deg_min", ctypes.c_int), ("deg_max", ctypes.c_int), ("opt_degree", ctypes.c_int),
                 ("eta", ctypes.c_double), ("cond_hi", ctypes.c_double), ("cond_lo", ctypes.c_double),
                 ("qr_force", ctypes.c_int), ("prec", ctypes.c_int), ("mp_switch", ctypes.c_double),
-                ("reserved", ctypes.c_int * 6)]
+                ("filtered_hook", ctypes.c_void_p), ("filtered_hook_ctx", ctypes.c_void_p),
+                ("cond_est_mode", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+FILTERED_HOOK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int)
 
 
 class Bounds(ctypes.Structure):
@@ -67,7 +72,8 @@ class IterLog(ctypes.Structure):
                 ("chol_fail_info", ctypes.c_int), ("deg_min", ctypes.c_int), ("deg_max", ctypes.c_int),
                 ("matvecs", ctypes.c_longlong), ("log_cond_est", ctypes.c_double),
                 ("c", ctypes.c_double), ("e", ctypes.c_double), ("mu1", ctypes.c_double),
-                ("mu_ell", ctypes.c_double)]
+                ("mu_ell", ctypes.c_double), ("log_cond_est_paper", ctypes.c_double),
+                ("log_cond_est_locked", ctypes.c_double)]
 
 
 _lib = None
@@ -179,6 +185,16 @@ class Handle:
         rc = lib().chase_reserve_workspace(self._h, int(nbytes))
         if rc:
             raise ChaseError(rc, "chase_reserve_workspace")
+
+
+def with_filtered_hook(cfg, fn):
+    """Attach fn(dX_ptr, n, ell, ldx, iteration) -- called after each filter with the device
+    block [Y V] about to be factored -- to cfg.  Keep the returned object alive while the
+    solve runs."""
+    cb = FILTERED_HOOK(lambda ctx, ptr, n, l, ld, it: fn(ptr, n, l, ld, it))
+    cfg.filtered_hook = ctypes.cast(cb, ctypes.c_void_p)
+    cfg.filtered_hook_ctx = None
+    return cb
 
 
 def chase_solve(h, A, V, nev, nex, bounds, cfg=None, log_cap=64, check=True):

@@ -557,9 +557,16 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     }
     if (rc) break;
     for (int a = k; a < l; ++a) matvecs += deg[a];
+    if (cfg.filtered_hook) {
+      CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+      cfg.filtered_hook(cfg.filtered_hook_ctx, V, n, l, n, it + 1);
+    }
     // --- condition estimate (Eq. full-est) and QR (Algorithm 3) ---
     const double theta_k1 = (it == 0) ? mu1 : ritz[k];
-    const double lest = log_cond_est(theta_k1, deg[k], deg[l - 1], mu1, c, e, cfg.eta);
+    const double lest_paper = log_cond_est(theta_k1, deg[k], deg[l - 1], mu1, c, e, cfg.eta);
+    const double lest_locked = std::max(
+        lest_paper, std::log(cfg.eta) + (double)deg[l - 1] * std::log(abs_rho(mu1, c, e)));
+    const double lest = (cfg.cond_est_mode == 1) ? lest_locked : lest_paper;
     phase_begin();
     if (k > 0) rc = copy_cols<T>(st, n, k, V, n, T2, n, &h->launches);
     int variant = 0, fi = 0;
@@ -617,6 +624,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       g.iteration = it + 1; g.locked_before = k; g.locked_after = knew; g.variant = variant;
       g.chol_fail_info = fi; g.deg_min = deg[k]; g.deg_max = deg[l - 1]; g.matvecs = matvecs;
       g.log_cond_est = lest; g.c = c; g.e = e; g.mu1 = mu1; g.mu_ell = mu_ell;
+      g.log_cond_est_paper = lest_paper; g.log_cond_est_locked = lest_locked;
     }
     for (int a = k; a < l; ++a) mu1 = std::min(mu1, ritz[a]);
     mu_ell = ritz[l - 1];
@@ -887,7 +895,8 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
   chase_config c;
   if (cfg) c = *cfg; else chase_config_default(&c);
   if (!(c.tol > 0.0) || c.max_iter < 0 || c.deg_init < 1 || c.deg_min < 1 || c.deg_max < c.deg_min ||
-      !(c.eta > 0.0) || c.qr_force < 0 || c.qr_force > 4)
+      !(c.eta > 0.0) || c.qr_force < 0 || c.qr_force > 4 || c.cond_est_mode < 0 ||
+      c.cond_est_mode > 1)
     return -8;
   if (c.prec != CHASE_FP64 && c.prec != CHASE_BF16X3 && c.prec != CHASE_FP64_EMU)
     return CHASE_ERR_UNSUPPORTED;

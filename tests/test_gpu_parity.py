@@ -298,3 +298,40 @@ def test_solve_without_bounds_runs_lanczos(cl, handle):
                                         cl.config_default(opt_degree=1, prec=cl.CHASE_FP64_EMU))
     assert rc == 0 and res.max() < prob.tol
     assert np.abs(ev - prob.lam[:prob.nev]).max() <= 1e-10 * np.abs(prob.lam).max()
+
+
+def test_condition_estimate_logs_match_oracle_and_bound_exact_kappa(cl, handle):
+    """Per iteration the solver's estimate (Eq. full-est) equals the oracle's and picks the
+    same QR variant; against the exact kappa_2 of the block [Y V] that Algorithm 3 factors
+    (read through the filtered-block hook): the printed estimate bounds it while no pair is
+    locked, the locked-aware form (cond_est_mode 1) in every iteration."""
+    import bench
+    prob = W.c2_complex_clustered(n=700, nev=30, nex=10, seed=14)
+    A_t = W.known_spectrum_matrix(prob.lam, prob.seed, True, device="cuda")
+    V0 = W.start_block(prob.n, prob.ell, prob.seed, True)
+    l1, le, bs = prob.bounds
+    kap = {}
+
+    def hook(ptr, n, l, ld, it):
+        X = bench.device_view(ptr, n, l, ld, True).cpu().numpy()
+        sv = np.linalg.svd(X, compute_uv=False)
+        kap[it] = math.log(sv[0] / sv[-1])
+
+    cfg = cl.config_default(opt_degree=1, prec=cl.CHASE_FP64_EMU)
+    keep = cl.with_filtered_hook(cfg, hook)
+    rc, ev, res, st, logs = cl.chase_solve(handle, A_t, dev(V0), prob.nev, prob.nex, prob.bounds, cfg)
+    del keep
+    ref = oracle.solve(host(A_t), V0, prob.nev, prob.nex, opt_degree=True, lambda1=l1,
+                       lambda_ell=le, b_sup=bs)
+    assert rc == 0 and len(kap) == st["iterations"] == ref["summary"]["iterations"]
+    locked_seen = False
+    for g, r in zip(logs, ref["logs"]):
+        assert g["variant"] == r["variant"]
+        assert abs(g["log_cond_est_paper"] - r["log_cond_est_paper"]) <= 1e-6 * max(1.0, abs(r["log_cond_est_paper"]))
+        assert g["log_cond_est"] == g["log_cond_est_paper"]          # default mode 0
+        assert g["log_cond_est_locked"] >= kap[g["iteration"]] - 1e-6
+        if g["locked_before"] == 0:
+            assert g["log_cond_est_paper"] >= kap[g["iteration"]] - 1e-6
+        else:
+            locked_seen = True
+    assert locked_seen

@@ -517,3 +517,29 @@ def test_lanczos_full_length_reproduces_the_spectrum():
     # fewer steps: interlacing Ritz values inside the spectrum
     (_, _, _), ritz = oracle.lanczos_bounds(A, V, n - 1, n)
     assert ritz.min() >= lam[0] - 1e-12 and ritz.max() <= lam[-1] + 1e-12
+
+
+@pytest.mark.parametrize("opt", [False, True])
+def test_condition_estimate_against_exact_kappa_per_iteration(opt):
+    """Figure 2's comparison on a synthetic spectrum, exact kappa_2 of [Y V] from the oracle's
+    one-sided Jacobi SVD before every QR.  Before any pair is locked the printed estimate
+    (Eq. full-est, eta = 1) bounds kappa_2 (Proposition th:2-2's regime); the locked-aware
+    form max(Eq. full-est, |rho_1|^{m_ell}) bounds it in every iteration; and both forms
+    coincide while nothing is locked."""
+    prob = W.c2_complex_clustered(n=360, nev=18, nex=6, seed=33)
+    A = W.known_spectrum_matrix(prob.lam, prob.seed, True).numpy()
+    V0 = W.start_block(prob.n, prob.ell, prob.seed, True)
+    l1, le, bs = prob.bounds
+    r = oracle.solve(A, V0, prob.nev, prob.nex, opt_degree=opt, lambda1=l1, lambda_ell=le,
+                     b_sup=bs, cond_est_mode=1, log_exact_kappa=True)
+    assert r["status"] == 0
+    locked_seen = False
+    for g in r["logs"]:
+        assert g["log_cond_est_locked"] >= g["log_cond_est_paper"]
+        assert g["log_cond_est_locked"] >= g["log_kappa_exact"] - 1e-9
+        if g["locked_before"] == 0:
+            assert g["log_cond_est_paper"] >= g["log_kappa_exact"] - 1e-9
+        else:
+            locked_seen = True
+        assert g["log_cond_est"] == g["log_cond_est_locked"]
+    assert locked_seen
