@@ -568,8 +568,9 @@ def main():
         "iterations": st["iterations"], "matvecs": st["matvecs"],
         "qr_variants": {"cholqr1": st["n_chol1"], "cholqr2": st["n_chol2"],
                         "shifted_cholqr2": st["n_shifted"], "householder": st["n_hhqr"]},
-        "phase_s": {k: st[k] for k in ("t_filter", "t_qr", "t_rr", "t_resid", "t_total",
+        "phase_s": {k: st[k] for k in ("t_filter", "t_qr", "t_rr", "t_rr_eig", "t_resid", "t_total",
                                         "t_filter_lowprec")},
+        "jacobi_sweeps": st["jacobi_sweeps"],
         "lowprec_iterations": st["n_lowprec_iters"],
         "iteration_log": [{"it": g["iteration"], "locked": g["locked_before"],
                            "variant": g["variant"], "log10_cond_est": g["log_cond_est"] / 2.302585092994046,

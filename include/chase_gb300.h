@@ -119,6 +119,8 @@ typedef struct {
   int n_lowprec_iters;     /* iterations whose filter ran in BF16x3 */
   double t_filter_lowprec; /* seconds of those filters */
   double filter_flops_lowprec; /* their algorithmic flops (counted as for FP64) */
+  double t_rr_eig;         /* part of t_rr spent in the Jacobi eigensolver */
+  int jacobi_sweeps;       /* Jacobi sweeps summed over iterations */
 } chase_stats;
 
 /* Per-iteration record (the kind of data Figure 2 plots). */

@@ -130,9 +130,10 @@ __device__ __forceinline__ void ld32(uint32_t taddr, uint32_t* r) {
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
-                   int M, int N, int nkb, int col0, const int* __restrict__ rowexp,
+                   int M, int N, int nkb_total, int kbs, int col0, const int* __restrict__ rowexp,
                    const int* __restrict__ colexp, double alpha, double beta, const double* X64,
-                   double gamma, const double* Z64, double* out64, int ldo, DevStatus* status) {
+                   double gamma, const double* Z64, double* out64, int ldo,
+                   double* __restrict__ partial, DevStatus* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* vst = smem;                          // 2 V stages
@@ -149,6 +150,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * OBN, m0 = blockIdx.y * OBM;
+  // split-K: this CTA's K blocks are [kbeg, kbeg + nkb), a whole number of exact chunks
+  const int kbeg = blockIdx.z * kbs;
+  const int nkb = max(0, min(kbs, nkb_total - kbeg));
   const int nchunks = (nkb + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
 
   if (threadIdx.x == 0) {
@@ -179,21 +183,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (!bar_wait(&vempty[vs], vph ^ 1)) { atomicOr(s_err, 1); break; }
       bar_expect(&vfull[vs], V_STAGE);
       for (int j = 0; j < OZ_S; ++j)
-        tma3(vst + vs * V_STAGE + j * V_TILE, &mapV, &vfull[vs], kb * OBK, col0 + n0, j);
+        tma3(vst + vs * V_STAGE + j * V_TILE, &mapV, &vfull[vs], (kbeg + kb) * OBK, col0 + n0, j);
       for (int i = 0; i < OZ_S; ++i, ++ai) {
         const int as = ai % OA_RING;
         const uint32_t aph = (uint32_t)((ai / OA_RING) & 1);
         if (!bar_wait(&aempty[as], aph ^ 1)) { atomicOr(s_err, 1); break; }
         bar_expect(&afull[as], A_TILE);
-        tma3(ast + as * A_TILE, &mapA, &afull[as], kb * OBK, m0, i);
+        tma3(ast + as * A_TILE, &mapA, &afull[as], (kbeg + kb) * OBK, m0, i);
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
+    // Fully unrolled: pair (i, j), level t = i + j, 4 K-steps of 16 per pair; the only
+    // runtime inputs per MMA are the chunk-start / first-block flags.
     int ai = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int chunk = kb / OZ_CHUNK_KB;
       const bool chunk_start = (kb % OZ_CHUNK_KB) == 0;
+      const bool first_kb = kb == 0;
       if (chunk_start && chunk > 0) {
         if (!bar_wait(cfree, (uint32_t)((chunk - 1) & 1))) { atomicOr(s_err, 2); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -201,27 +208,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int vs = kb & 1;
       if (!bar_wait(&vfull[vs], (uint32_t)((kb >> 1) & 1))) { atomicOr(s_err, 2); break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t vbase = s32(vst + vs * V_STAGE);
+      const uint64_t dv0 = desc_sw128(s32(vst + vs * V_STAGE));
       bool bad = false;
-      for (int i = 1; i <= OZ_S; ++i, ++ai) {
+#pragma unroll
+      for (int i = 1; i <= OZ_S; ++i) {
         const int as = ai % OA_RING;
         if (!bar_wait(&afull[as], (uint32_t)((ai / OA_RING) & 1))) { bad = true; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint64_t da = desc_sw128(s32(ast + as * A_TILE));
+#pragma unroll
         for (int j = 1; j <= OZ_S + 1 - i; ++j) {
           const int t = i + j;
           const uint32_t dcol = tmem + (uint32_t)((t - 2) * OBN);
-          const uint64_t dv = desc_sw128(vbase + (uint32_t)((j - 1) * V_TILE));
+          const uint64_t dv = dv0 + (uint64_t)(((j - 1) * V_TILE) >> 4);
+          const bool restart_flag = (t <= 5) ? chunk_start : first_kb;
 #pragma unroll
           for (int kk = 0; kk < OBK / 16; ++kk) {
             const uint64_t off = (uint64_t)((kk * 32) >> 4);
-            // levels 2..5 restart every chunk, levels 6..9 accumulate over all of K;
-            // pair (1, t-1) is the first product of level t in each pass
-            const bool restart = (i == 1 && kk == 0) && (t <= 5 ? chunk_start : kb == 0);
-            mma(dcol, da + off, dv + off, restart ? 0u : 1u);
+            const uint32_t acc = (i == 1 && kk == 0 && restart_flag) ? 0u : 1u;
+            mma(dcol, da + off, dv + off, acc);
           }
         }
         commit(&aempty[as]);
+        ++ai;
       }
       if (bad) { atomicOr(s_err, 2); break; }
       commit(&vempty[vs]);
@@ -252,13 +261,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (lane == 0 && c + 1 < nchunks) bar_arrive(cfree);
     }
     const int r = m0 + 32 * q + lane;
+    if (nkb == 0) ok = true;  // empty split: contributes zeros
     if (ok && !*(volatile int*)s_err) {
       // levels 6..9 (FP32 over the whole K), combined with level sum 2..5 in FP64
       double y[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) y[j] = 0.0;
 #pragma unroll 1
-      for (int t = 9; t >= 6; --t) {
+      for (int t = 9; t >= 6 && nkb > 0; --t) {
         uint32_t rr[32];
         ld32(tbase + (uint32_t)((t - 2) * OBN), rr);
         const double w = ldexp(1.0, -OZ_B * (t - 5));  // relative to the 2..5 sum's unit
@@ -273,7 +283,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           if (c >= N) break;
           const int e = er + colexp[col0 + c];
           // value = 2^{e} 2^{-35} (G1 + sum_{t>=6} 2^{-7(t-5)} L_t)
-          const double v0 = ldexp((double)g1[j] + y[j], e - OZ_B * 5);
+          const double v0 = (nkb == 0) ? 0.0 : ldexp((double)g1[j] + y[j], e - OZ_B * 5);
+          if (partial) {
+            partial[(size_t)blockIdx.z * M * N + (size_t)r + (size_t)c * M] = v0;
+            continue;
+          }
           const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
           double v = alpha * v0;
           if (beta != 0.0) v = fma(beta, X64[idx], v);
@@ -290,6 +304,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
   if (threadIdx.x == 0 && *s_err) atomicOr(&status->timeout, *s_err);
+}
+
+// Sum of the split-K partial results in a fixed order, then the three-term epilogue.
+__global__ void oz_reduce_kernel(int M, int N, int S, const double* __restrict__ P, int col0,
+                                 double alpha, double beta, const double* X64, double gamma,
+                                 const double* Z64, double* out64, int ldo) {
+  const size_t total = (size_t)M * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % M), c = (int)(t / M);
+    double y = 0.0;
+    for (int z = 0; z < S; ++z) y += P[(size_t)z * total + t];
+    const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
+    double v = alpha * y;
+    if (beta != 0.0) v = fma(beta, X64[idx], v);
+    if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
+    out64[idx] = v;
+  }
 }
 
 // ---------------- slicing ----------------
@@ -454,17 +486,34 @@ int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ld
 int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
             const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
-            DevStatus* dst, int* launches) {
+            DevStatus* dst, Scratch scr, int* launches) {
   if (N <= 0) return 0;
   CUtensorMap mA, mV;
   if (make_map3(&mA, Aplanes, kp, M, OBM) || make_map3(&mV, Vplanes, kp, ncols_total, OBN))
     return CHASE_ERR_CUDA;
   CHASE_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       OZ_SMEM));
-  dim3 grid(ceil_div(N, OBN), ceil_div(M, OBM));
-  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, st>>>(mA, mV, M, N, kp / OBK, col0, rowexp, colexp,
-                                                    alpha, beta, X64, gamma, Z64, out64, ldo, dst);
+  const int nkb = kp / OBK;
+  const int tiles = ceil_div(N, OBN) * ceil_div(M, OBM);
+  // split K (in whole exact chunks) until there are about four waves of CTAs
+  const int nchunks = ceil_div(nkb, OZ_CHUNK_KB);
+  int S = std::max(1, std::min(nchunks, ceil_div(4 * kNumSMs, tiles)));
+  while (S > 1 && (size_t)S * M * N * sizeof(double) > scr.bytes) --S;
+  const int kbs = ceil_div(nchunks, S) * OZ_CHUNK_KB;
+  S = ceil_div(nkb, kbs);
+  double* partial = (S > 1) ? (double*)scr.ptr : nullptr;
+  dim3 grid(ceil_div(N, OBN), ceil_div(M, OBM), S);
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, st>>>(mA, mV, M, N, nkb, kbs, col0, rowexp, colexp,
+                                                    alpha, beta, X64, gamma, Z64, out64, ldo,
+                                                    partial, dst);
   if (launches) ++*launches;
+  if (S > 1) {
+    const size_t total = (size_t)M * N;
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16);
+    oz_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, S, partial, col0, alpha, beta, X64, gamma, Z64,
+                                             out64, ldo);
+    if (launches) ++*launches;
+  }
   CHASE_CUDA_TRY(cudaGetLastError());
   return 0;
 }

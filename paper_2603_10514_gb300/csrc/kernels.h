@@ -105,7 +105,7 @@ int oz_stack_V(cudaStream_t st, int n, int ncols, const T* V, int ldv, double* V
 int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
             const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
-            DevStatus* dst, int* launches);
+            DevStatus* dst, Scratch scr, int* launches);
 
 // ---- Lanczos spectral bounds (lanczos.cu) ----------------------------------
 // out = {lambda1, lambda_ell, b_sup} from nruns runs of m steps started at V0's columns.

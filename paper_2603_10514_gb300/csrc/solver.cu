@@ -305,8 +305,8 @@ OzBufs oz_carve(char* base, int n, int ncols) {
 
 template <class T>
 int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols, T* V, int ldv,
-              const int* deg, double c, double e, double lambda1, OzBufs& B, double* flops,
-              int* steps) {
+              const int* deg, double c, double e, double lambda1, OzBufs& B, Scratch scr,
+              double* flops, int* steps) {
   cudaStream_t st = h->stream;
   if (ncols <= 0) return 0;
   const int M = B.M, kp = B.kp;
@@ -336,7 +336,7 @@ int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols,
     }
     TRY(oz_slice_V(st, M, first, ncols, B.V64[in], kp, kp, ncols, B.Vp, B.colexp, &h->launches));
     TRY(oz_gemm(st, M, kp, B.Ap, B.rowexp, B.Vp, B.colexp, ncols, first, act, alpha, beta,
-                B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, &h->launches));
+                B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, scr, &h->launches));
     if (flops) *flops += per_col * act;
     if (steps) ++*steps;
   }
@@ -355,13 +355,13 @@ int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols,
 
 // AQ = A Q (n x nu, both ld n) by the Ozaki-scheme product; A's planes must be ready.
 template <class T>
-int aq_oz(chase_ctx* h, int n, const T* Q, int nu, T* AQ, OzBufs& B) {
+int aq_oz(chase_ctx* h, int n, const T* Q, int nu, T* AQ, OzBufs& B, Scratch scr) {
   cudaStream_t st = h->stream;
   if (nu <= 0) return 0;
   TRY(oz_stack_V<T>(st, n, nu, Q, n, B.V64[0], B.kp, &h->launches));
   TRY(oz_slice_V(st, B.M, 0, nu, B.V64[0], B.kp, B.kp, B.ncols, B.Vp, B.colexp, &h->launches));
   TRY(oz_gemm(st, B.M, B.kp, B.Ap, B.rowexp, B.Vp, B.colexp, B.ncols, 0, nu, 1.0, 0.0, nullptr,
-              0.0, nullptr, B.V64[1], B.kp, h->dstat, &h->launches));
+              0.0, nullptr, B.V64[1], B.kp, h->dstat, scr, &h->launches));
   TRY(tc_unstack_V<T>(st, n, 0, nu, B.V64[1], B.kp, AQ, n, &h->launches));
   return 0;
 }
@@ -547,7 +547,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       ++S.n_lowprec_iters;
     } else if (emu) {
       rc = filter_oz<T>(h, n, A, lda, !A_oz, nu, V + (size_t)k * n, n, deg.data() + k, c, e, mu1,
-                        ozb, &S.filter_flops, &S.filter_launches);
+                        ozb, scr, &S.filter_flops, &S.filter_launches);
       A_oz = true;
       phase_end(S.t_filter);
     } else {
@@ -586,7 +586,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     if (emu) {
       if (!A_oz) rc = oz_slice_A<T>(st, n, A, lda, ozb.kp, ozb.Ap, ozb.rowexp, &h->launches);
       A_oz = true;
-      if (!rc) rc = aq_oz<T>(h, n, Q2, nu, AQ, ozb);
+      if (!rc) rc = aq_oz<T>(h, n, Q2, nu, AQ, ozb, scr);
     } else {
       rc = gemm<T>(st, false, n, nu, n, A, lda, Q2, n, AQ, n, 1.0, 0.0, nullptr, 0, 0.0, nullptr,
                    0, scr, false, false, &h->launches);
@@ -595,7 +595,17 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
                           nullptr, 0, scr, true, false, &h->launches);
     if (!rc) rc = herm_fill_lower<T>(st, nu, H, nu, &h->launches);
     int sweeps = 0;
+    cudaEvent_t j0, j1;
+    cudaEventCreate(&j0);
+    cudaEventCreate(&j1);
+    cudaEventRecord(j0, st);
     if (!rc) rc = jacobi_eig<T>(st, nu, H, nu, Wm, nu, dw, jac, jac_bytes, 40, &sweeps, &h->launches);
+    cudaEventRecord(j1, st);
+    cudaEventSynchronize(j1);
+    S.t_rr_eig += elapsed_s(j0, j1);
+    S.jacobi_sweeps += sweeps;
+    cudaEventDestroy(j0);
+    cudaEventDestroy(j1);
     // V <- Q2 W (via T2), AV = AQ W (into P)
     if (!rc) rc = gemm<T>(st, false, n, nu, nu, Q2, n, Wm, nu, T2, n, 1.0, 0.0, nullptr, 0, 0.0,
                           nullptr, 0, scr, false, false, &h->launches);
@@ -723,11 +733,13 @@ int filter_impl(chase_ctx* h, int n, const T* A, int lda, int ncols, const T* dV
                 T* dVout, int ldo) {
   cudaStream_t st = h->stream;
   if (prec == CHASE_FP64_EMU) {
-    TRY(ensure_ws(h, oz_bytes<T>(n, ncols)));
+    const size_t ob = align256(oz_bytes<T>(n, ncols));
+    TRY(ensure_ws(h, ob + kScratchBytes));
     OzBufs B = oz_carve<T>((char*)h->ws, n, ncols);
+    Scratch scr{(char*)h->ws + ob, kScratchBytes};
     if (dVout != dV) TRY(copy_cols<T>(st, n, ncols, dV, ldv, dVout, ldo, &h->launches));
     double fl = 0.0;
-    return filter_oz<T>(h, n, A, lda, true, ncols, dVout, ldo, degrees, c, e, lambda1, B, &fl,
+    return filter_oz<T>(h, n, A, lda, true, ncols, dVout, ldo, degrees, c, e, lambda1, B, scr, &fl,
                         nullptr);
   }
   if (prec == CHASE_BF16X3) {
