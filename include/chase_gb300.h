@@ -205,6 +205,21 @@ int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int 
              double est_cond, int qr_force, int* variant_used, int* chol_info);
 
 /*
+ * chase_qr_prec -- chase_qr with a choice of arithmetic for its two block
+ * products (the Gram matrix X^H X and X R^{-1}; Algorithm 2):
+ *   CHASE_FP64      FP64 CUDA-core products (chase_qr);
+ *   CHASE_FP64_EMU  Ozaki-scheme products on the BF16 tensor cores, accurate
+ *                   to the FP64 error class (the products chase_solve uses in
+ *                   that precision).
+ * The Cholesky factor, its inverse and the Householder fallback stay FP64.
+ * Other precisions return -9.  Workspace grows by about 16 (2n or n) ncols
+ * bytes of digit planes in the emulated mode.
+ */
+int chase_qr_prec(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int ldx,
+                  double est_cond, int qr_force, chase_precision prec, int* variant_used,
+                  int* chol_info);
+
+/*
  * chase_cond_est -- the estimate of Eq. full-est (Corollary cr:3-1):
  *   kappa_est = eta |rho_{k+1}|^{m_{k+1}} |rho_1|^{m_ell - m_{k+1}},
  * |rho(x)| = |t| + sqrt(t^2 - 1), t = (x - c)/e (1 inside the damped interval).

@@ -28,7 +28,8 @@ CHASE_FILTER_NOALLOC_MAX_BYTES = 32 << 20
 QR_VARIANTS = {1: "cholqr1", 2: "cholqr2", 3: "shifted_cholqr2", 4: "householder"}
 
 EXPORTED = ["chase_create", "chase_destroy", "chase_config_default", "chase_workspace_bytes",
-            "chase_solve", "chase_filter", "chase_qr", "chase_cond_est", "chase_status_string",
+            "chase_solve", "chase_filter", "chase_qr", "chase_qr_prec", "chase_cond_est",
+            "chase_status_string",
             "chase_filter_noalloc", "chase_reserve_workspace", "chase_lanczos_bounds"]
 
 
@@ -105,6 +106,7 @@ def lib():
                                   P, i, P, P, ctypes.POINTER(Stats), P, i]
         L.chase_filter.argtypes = [P, i, i, P, i, i, P, i, P, d, d, d, i, P, i]
         L.chase_qr.argtypes = [P, i, i, i, P, i, d, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.chase_qr_prec.argtypes = [P, i, i, i, P, i, d, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.chase_cond_est.argtypes = [i, i, P, P, d, d, d, d, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.chase_filter_noalloc.argtypes = [i, i, P, i, i, P, i, P, d, d, d, P, i, P]
         L.chase_status_string.argtypes = [i]
@@ -244,14 +246,20 @@ def chase_filter(h, A, V, degrees, c, e, lambda1, out=None, prec=CHASE_FP64):
     return out
 
 
-def chase_qr(h, X, est_cond, qr_force=0, check=True):
-    """Algorithm 3 in place on the CUDA tensor X.  Returns (status, variant, chol_info)."""
+def chase_qr(h, X, est_cond, qr_force=0, check=True, prec=None):
+    """Algorithm 3 in place on the CUDA tensor X.  Returns (status, variant, chol_info).
+    prec=None calls chase_qr (FP64 products); otherwise chase_qr_prec."""
     n, l = X.shape
     dt = _dtype_code(X)
     ldx = _ld(X, "X")
     v, info = ctypes.c_int(0), ctypes.c_int(0)
-    rc = lib().chase_qr(h.ptr, dt, n, l, ctypes.c_void_p(X.data_ptr()), ldx, float(est_cond),
-                        int(qr_force), ctypes.byref(v), ctypes.byref(info))
+    if prec is None:
+        rc = lib().chase_qr(h.ptr, dt, n, l, ctypes.c_void_p(X.data_ptr()), ldx, float(est_cond),
+                            int(qr_force), ctypes.byref(v), ctypes.byref(info))
+    else:
+        rc = lib().chase_qr_prec(h.ptr, dt, n, l, ctypes.c_void_p(X.data_ptr()), ldx,
+                                 float(est_cond), int(qr_force), int(prec), ctypes.byref(v),
+                                 ctypes.byref(info))
     if check and rc not in (CHASE_OK, CHASE_CHOL_FAILED):
         raise ChaseError(rc, "chase_qr")
     return rc, v.value, info.value

@@ -432,6 +432,112 @@ __global__ void stack_V_kernel(int n, int ncols, const T* __restrict__ V, int ld
   }
 }
 
+// Xt (l x n, ld ldt) is the transpose of a column-major X (n x l): row m of X is column m
+// of Xt.  Digits of the rows of the stacked operator [[Xr, -Xi], [Xi, Xr]] (2n x 2l; real:
+// X itself, n x l) into planes (row-major, ld kp), row exponents into rowexp.
+template <class T>
+__global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, int l, const T* __restrict__ Xt,
+                                                            int ldt, int kp, __nv_bfloat16* planes,
+                                                            size_t plane, int* rowexp) {
+  __shared__ double red[8];
+  const int m = blockIdx.x;
+  const int mm = Sc<T>::cplx ? (m % n) : m;
+  const bool mre = !Sc<T>::cplx || m < n;
+  const int K = Sc<T>::cplx ? 2 * l : l;
+  const T* row = Xt + (size_t)mm * ldt;  // X[mm, 0..l)
+  auto elem = [&](int k) -> double {
+    if constexpr (Sc<T>::cplx) {
+      const z64 x = row[k % l];
+      const bool kre = k < l;
+      // [[Xr, -Xi], [Xi, Xr]]
+      return mre ? (kre ? x.x : -x.y) : (kre ? x.y : x.x);
+    } else {
+      return row[k];
+    }
+  };
+  double amax = 0.0;
+  for (int k = threadIdx.x; k < K; k += 256) amax = fmax(amax, fabs(elem(k)));
+  amax = block_max(amax, red);
+  const int e = exp_bound(amax);
+  if (threadIdx.x == 0) rowexp[m] = e;
+  for (int k = threadIdx.x; k < kp; k += 256) {
+    const double x = (k < K) ? elem(k) : 0.0;
+    write_digits(x, e, planes, (size_t)m * kp + k, plane);
+  }
+}
+
+// Digits of the columns of a block Y (n x q, ld ldy) in stacked form: plane column j < q
+// holds [Re Y; Im Y][:, j]; with `pair` (complex only) plane column q + j holds the stacked
+// -i Y[:, j] = [Im Y; -Re Y][:, j].  Then, with X's columns as the left operand's rows,
+// Xhat^T [Yhat | stack(-i Y)] = [Re(X^H Y) | Im(X^H Y)].  Both columns of a pair share the
+// exponent of Y[:, j].  Planes column-major (ld kp; rows >= M are zero).
+template <class T>
+__global__ void __launch_bounds__(512) oz_slice_cols_kernel(int n, int q, const T* __restrict__ Y,
+                                                            int ldy, int kp, bool pair,
+                                                            __nv_bfloat16* planes, size_t plane,
+                                                            int* colexp) {
+  __shared__ double red[16];
+  const int j = blockIdx.x;
+  const int M = Sc<T>::cplx ? 2 * n : n;
+  const T* col = Y + (size_t)j * ldy;
+  double amax = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if constexpr (Sc<T>::cplx) amax = fmax(amax, fmax(fabs(col[i].x), fabs(col[i].y)));
+    else amax = fmax(amax, fabs(col[i]));
+  }
+  amax = block_max(amax, red);
+  const int e = exp_bound(amax);
+  if (threadIdx.x == 0) {
+    colexp[j] = e;
+    if (pair) colexp[q + j] = e;
+  }
+  for (int k = threadIdx.x; k < kp; k += blockDim.x) {
+    double x = 0.0, y = 0.0;
+    if (k < M) {
+      if constexpr (Sc<T>::cplx) {
+        const z64 v = col[k % n];
+        x = (k < n) ? v.x : v.y;
+        y = (k < n) ? v.y : -v.x;
+      } else {
+        x = col[k];
+      }
+    }
+    write_digits(x, e, planes, (size_t)j * kp + k, plane);
+    if (pair) write_digits(y, e, planes, (size_t)(q + j) * kp + k, plane);
+  }
+}
+
+// out (l x 2l FP64, ld ldo) -> G (l x l, ld ldg) with G = out[:, :l] + i out[:, l:] (real: copy)
+template <class T>
+__global__ void gram_assemble_kernel(int l, const double* __restrict__ out, int ldo, T* G, int ldg) {
+  const size_t total = (size_t)l * l;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(t % l), q = (int)(t / l);
+    if constexpr (Sc<T>::cplx) {
+      G[(size_t)p + (size_t)q * ldg] = z64{out[(size_t)p + (size_t)q * ldo], out[(size_t)p + (size_t)(q + l) * ldo]};
+    } else {
+      G[(size_t)p + (size_t)q * ldg] = out[(size_t)p + (size_t)q * ldo];
+    }
+  }
+}
+
+// Xt = X^T (plain transpose, no conjugation): X n x l (ld ldx) -> Xt l x n (ld ldt).
+template <class T>
+__global__ void transpose_kernel(int n, int l, const T* __restrict__ X, int ldx, T* Xt, int ldt) {
+  __shared__ T tile[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + threadIdx.x, j = j0 + r;
+    if (i < n && j < l) tile[r][threadIdx.x] = X[(size_t)i + (size_t)j * ldx];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + threadIdx.x, i = i0 + r;
+    if (i < n && j < l) Xt[(size_t)j + (size_t)i * ldt] = tile[threadIdx.x][r];
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -444,12 +550,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-// 3-D BF16 map over S digit planes: {kp (contiguous), rows, S}, box {64, box_rows, 1}.
-int make_map3(CUtensorMap* map, const void* base, int kp, int rows, int box_rows) {
+// 3-D BF16 map over S digit planes: {kp (contiguous), rows, S}, box {64, box_rows, 1};
+// consecutive planes are plane_rows * kp elements apart (plane_rows >= rows).
+int make_map3(CUtensorMap* map, const void* base, int kp, int rows, int plane_rows, int box_rows) {
   auto enc = encoder();
   if (!enc) return CHASE_ERR_CUDA;
   cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)OZ_S};
-  cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * 2 * (cuuint64_t)rows};
+  cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * 2 * (cuuint64_t)plane_rows};
   cuuint32_t box[3] = {OBK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
@@ -484,12 +591,14 @@ int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ld
 }
 
 int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
-            const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
+            int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
             DevStatus* dst, Scratch scr, int* launches) {
   if (N <= 0) return 0;
   CUtensorMap mA, mV;
-  if (make_map3(&mA, Aplanes, kp, M, OBM) || make_map3(&mV, Vplanes, kp, ncols_total, OBN))
+  if (a_plane_rows < M) a_plane_rows = M;
+  if (make_map3(&mA, Aplanes, kp, M, a_plane_rows, OBM) ||
+      make_map3(&mV, Vplanes, kp, ncols_total, ncols_total, OBN))
     return CHASE_ERR_CUDA;
   CHASE_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       OZ_SMEM));
@@ -530,6 +639,59 @@ int oz_stack_V(cudaStream_t st, int n, int ncols, const T* V, int ldv, double* V
   CHASE_CUDA_TRY(cudaGetLastError());
   return 0;
 }
+
+template <class T>
+int oz_slice_rows(cudaStream_t st, int n, int l, const T* Xt, int ldt, int kp, void* planes,
+                  int* rowexp, int* launches) {
+  const int M = Sc<T>::cplx ? 2 * n : n;
+  oz_slice_rows_kernel<T><<<M, 256, 0, st>>>(n, l, Xt, ldt, kp, (__nv_bfloat16*)planes,
+                                             (size_t)M * kp, rowexp);
+  if (launches) ++*launches;
+  CHASE_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+template <class T>
+int oz_slice_cols(cudaStream_t st, int n, int q, const T* Y, int ldy, int kp, bool pair,
+                  void* planes, int* colexp, int* launches) {
+  if (q <= 0) return 0;
+  pair = pair && Sc<T>::cplx;
+  const size_t ncols_total = pair ? 2 * (size_t)q : (size_t)q;
+  oz_slice_cols_kernel<T><<<q, 512, 0, st>>>(n, q, Y, ldy, kp, pair, (__nv_bfloat16*)planes,
+                                             ncols_total * kp, colexp);
+  if (launches) ++*launches;
+  CHASE_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+template <class T>
+int oz_gram_assemble(cudaStream_t st, int l, const double* out, int ldo, T* G, int ldg, int* launches) {
+  const size_t work = (size_t)l * l;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((work + 255) / 256, (size_t)kNumSMs * 16));
+  gram_assemble_kernel<T><<<blocks, 256, 0, st>>>(l, out, ldo, G, ldg);
+  if (launches) ++*launches;
+  CHASE_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+template <class T>
+int transpose(cudaStream_t st, int n, int l, const T* X, int ldx, T* Xt, int ldt, int* launches) {
+  dim3 grid(ceil_div(n, 32), ceil_div(l, 32)), block(32, 8);
+  transpose_kernel<T><<<grid, block, 0, st>>>(n, l, X, ldx, Xt, ldt);
+  if (launches) ++*launches;
+  CHASE_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+#define OZ_INST(T)                                                                                \
+  template int oz_slice_rows<T>(cudaStream_t, int, int, const T*, int, int, void*, int*, int*);   \
+  template int oz_slice_cols<T>(cudaStream_t, int, int, const T*, int, int, bool, void*, int*,   \
+                                int*);                                                            \
+  template int oz_gram_assemble<T>(cudaStream_t, int, const double*, int, T*, int, int*);         \
+  template int transpose<T>(cudaStream_t, int, int, const T*, int, T*, int, int*);
+OZ_INST(double)
+OZ_INST(z64)
+#undef OZ_INST
 
 template int oz_stack_V<double>(cudaStream_t, int, int, const double*, int, double*, int, int*);
 template int oz_stack_V<z64>(cudaStream_t, int, int, const z64*, int, double*, int, int*);

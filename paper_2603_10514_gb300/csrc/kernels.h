@@ -101,9 +101,24 @@ int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ld
 template <class T>
 int oz_stack_V(cudaStream_t st, int n, int ncols, const T* V, int ldv, double* V64, int ldo,
                int* launches);
+// Row digits of the stacked operator of a general X given as Xt = X^T (l x n, ld ldt).
+template <class T>
+int oz_slice_rows(cudaStream_t st, int n, int l, const T* Xt, int ldt, int kp, void* planes,
+                  int* rowexp, int* launches);
+// Column digits of a block Y (n x q): plane column j = stacked Y[:, j] and, with pair
+// (complex only), plane column q + j = stacked (-i Y[:, j]); plane stride (q or 2q) * kp.
+template <class T>
+int oz_slice_cols(cudaStream_t st, int n, int q, const T* Y, int ldy, int kp, bool pair,
+                  void* planes, int* colexp, int* launches);
+// G = out[:, :l] + i out[:, l:] (complex) or out (real); out l x 2l (or l x l), ld ldo.
+template <class T>
+int oz_gram_assemble(cudaStream_t st, int l, const double* out, int ldo, T* G, int ldg, int* launches);
+template <class T>
+int transpose(cudaStream_t st, int n, int l, const T* X, int ldx, T* Xt, int ldt, int* launches);
 // out64[:, col0 + c] = alpha * (A V)[:, col0 + c] + beta * X64 + gamma * Z64 for c < N.
+// A's planes are a_plane_rows * kp elements apart (0: M * kp).
 int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
-            const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
+            int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
             DevStatus* dst, Scratch scr, int* launches);
 

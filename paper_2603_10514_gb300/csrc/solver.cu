@@ -335,7 +335,7 @@ int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols,
       sigma = sn;
     }
     TRY(oz_slice_V(st, M, first, ncols, B.V64[in], kp, kp, ncols, B.Vp, B.colexp, &h->launches));
-    TRY(oz_gemm(st, M, kp, B.Ap, B.rowexp, B.Vp, B.colexp, ncols, first, act, alpha, beta,
+    TRY(oz_gemm(st, M, kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, ncols, first, act, alpha, beta,
                 B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, scr, &h->launches));
     if (flops) *flops += per_col * act;
     if (steps) ++*steps;
@@ -360,20 +360,127 @@ int aq_oz(chase_ctx* h, int n, const T* Q, int nu, T* AQ, OzBufs& B, Scratch scr
   if (nu <= 0) return 0;
   TRY(oz_stack_V<T>(st, n, nu, Q, n, B.V64[0], B.kp, &h->launches));
   TRY(oz_slice_V(st, B.M, 0, nu, B.V64[0], B.kp, B.kp, B.ncols, B.Vp, B.colexp, &h->launches));
-  TRY(oz_gemm(st, B.M, B.kp, B.Ap, B.rowexp, B.Vp, B.colexp, B.ncols, 0, nu, 1.0, 0.0, nullptr,
+  TRY(oz_gemm(st, B.M, B.kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, B.ncols, 0, nu, 1.0, 0.0, nullptr,
               0.0, nullptr, B.V64[1], B.kp, h->dstat, scr, &h->launches));
   TRY(tc_unstack_V<T>(st, n, 0, nu, B.V64[1], B.kp, AQ, n, &h->launches));
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// FP64-accurate products of the QR and Rayleigh-Ritz steps by the Ozaki scheme:
+//   Gram    G = X^H Y (l x l; X's columns are the left operand's rows, Y and
+//           -i Y the right operand's columns, K = n or 2n);
+//   tall    Y = X B  (X n x kl sliced by rows of its stacked operator
+//           [[Xr, -Xi], [Xi, Xr]], B kl x N stacked as [Br; Bi]).
+// ---------------------------------------------------------------------------
+struct OzProd {
+  int n = 0, l = 0, M = 0, kp = 0, kpl = 0;
+  void* Gp = nullptr;  int* gexp = nullptr;   // kp x 2l column planes (Y | -iY)
+  void* Lp = nullptr;  int* lexp = nullptr;   // kp x l column planes (X, when X != Y)
+  void* Rp = nullptr;  int* rexp = nullptr;   // M x kpl row planes of a tall X
+  void* Bp = nullptr;  int* bexp = nullptr;   // kpl x l column planes of a small factor
+  double* B64 = nullptr;                      // kpl x l stacked small factor
+  double* out = nullptr;                      // FP64 result staging, max(M, 2l) x l
+  void* Xt = nullptr;                         // X^T (l x n)
+};
+
+template <class T>
+size_t ozp_bytes(int n, int l) {
+  const int M = Sc<T>::cplx ? 2 * n : n;
+  const size_t kp = (size_t)tc_kpad(M);
+  const size_t kpl = (size_t)tc_kpad(Sc<T>::cplx ? 2 * l : l);
+  const size_t wl = Sc<T>::cplx ? 2 * (size_t)l : (size_t)l;
+  return align256(16 * kp * wl) + align256(4 * wl) + align256(16 * kp * l) + align256(4 * (size_t)l) +
+         align256(16 * (size_t)M * kpl) + align256(4 * (size_t)M) + align256(16 * kpl * l) +
+         align256(4 * (size_t)l) + align256(8 * kpl * l) +
+         align256(8 * std::max<size_t>(M, wl) * l) + align256(sizeof(T) * (size_t)n * l);
+}
+
+template <class T>
+OzProd ozp_carve(char* base, int n, int l) {
+  OzProd P;
+  P.n = n; P.l = l;
+  P.M = Sc<T>::cplx ? 2 * n : n;
+  P.kp = tc_kpad(P.M);
+  P.kpl = tc_kpad(Sc<T>::cplx ? 2 * l : l);
+  const size_t wl = Sc<T>::cplx ? 2 * (size_t)l : (size_t)l;
+  size_t off = 0;
+  auto take = [&](size_t b) { char* p = base + off; off += align256(b); return p; };
+  P.Gp = take(16 * (size_t)P.kp * wl);
+  P.gexp = (int*)take(4 * wl);
+  P.Lp = take(16 * (size_t)P.kp * l);
+  P.lexp = (int*)take(4 * (size_t)l);
+  P.Rp = take(16 * (size_t)P.M * P.kpl);
+  P.rexp = (int*)take(4 * (size_t)P.M);
+  P.Bp = take(16 * (size_t)P.kpl * l);
+  P.bexp = (int*)take(4 * (size_t)l);
+  P.B64 = (double*)take(8 * (size_t)P.kpl * l);
+  P.out = (double*)take(8 * std::max<size_t>(P.M, wl) * l);
+  P.Xt = take(sizeof(T) * (size_t)n * l);
+  return P;
+}
+
+// G = X^H Y (q x q, ld ldg) for X, Y n x q; X == Y uses one slicing for both sides.
+template <class T>
+int oz_gram(chase_ctx* h, OzProd& P, int q, const T* X, int ldx, const T* Y, int ldy, T* G, int ldg,
+            Scratch scr) {
+  cudaStream_t st = h->stream;
+  if (q <= 0) return 0;
+  const bool cplx = Sc<T>::cplx;
+  const int wq = cplx ? 2 * q : q;
+  TRY(oz_slice_cols<T>(st, P.n, q, Y, ldy, P.kp, true, P.Gp, P.gexp, &h->launches));
+  const void* left = P.Gp;
+  const int* lexp = P.gexp;
+  int plane_rows = wq;
+  if (X != Y) {
+    TRY(oz_slice_cols<T>(st, P.n, q, X, ldx, P.kp, false, P.Lp, P.lexp, &h->launches));
+    left = P.Lp;
+    lexp = P.lexp;
+    plane_rows = q;
+  }
+  TRY(oz_gemm(st, q, P.kp, left, lexp, plane_rows, P.Gp, P.gexp, wq, 0, wq, 1.0, 0.0, nullptr, 0.0,
+              nullptr, P.out, q, h->dstat, scr, &h->launches));
+  TRY(oz_gram_assemble<T>(st, q, P.out, q, G, ldg, &h->launches));
+  return 0;
+}
+
+// Digit planes of the small right factor B (kl x N, ld ldb) for oz_tall.
+template <class T>
+int oz_prep_factor(chase_ctx* h, OzProd& P, int kl, int N, const T* B, int ldb) {
+  cudaStream_t st = h->stream;
+  const int K = Sc<T>::cplx ? 2 * kl : kl;
+  TRY(oz_stack_V<T>(st, kl, N, B, ldb, P.B64, P.kpl, &h->launches));
+  TRY(oz_slice_V(st, K, 0, N, P.B64, P.kpl, P.kpl, N, P.Bp, P.bexp, &h->launches));
+  return 0;
+}
+
+// Y = X B (n x N, ld ldy) with X n x kl (ld ldx) and B prepared by oz_prep_factor.
+// Y may alias X: X is fully sliced before Y is written.
+template <class T>
+int oz_tall(chase_ctx* h, OzProd& P, int kl, const T* X, int ldx, int N, T* Y, int ldy, Scratch scr) {
+  cudaStream_t st = h->stream;
+  if (N <= 0) return 0;
+  T* Xt = (T*)P.Xt;
+  TRY(transpose<T>(st, P.n, kl, X, ldx, Xt, kl, &h->launches));
+  TRY(oz_slice_rows<T>(st, P.n, kl, Xt, kl, P.kpl, P.Rp, P.rexp, &h->launches));
+  TRY(oz_gemm(st, P.M, P.kpl, P.Rp, P.rexp, 0, P.Bp, P.bexp, N, 0, N, 1.0, 0.0, nullptr, 0.0,
+              nullptr, P.out, P.M, h->dstat, scr, &h->launches));
+  TRY(tc_unstack_V<T>(st, P.n, 0, N, P.out, P.M, Y, ldy, &h->launches));
+  return 0;
+}
+
 // One CholeskyQR pass (Algorithm 2 body): X <- X R^{-1} with R = chol(X^H X [+ sI]).
 // Result lands in X (via Xtmp).  Returns 0, CHASE_CHOL_FAILED (info in *info) or an error.
+// With oz the two products run as Ozaki-scheme products.
 template <class T>
 int cholqr_pass(chase_ctx* h, int n, int l, T* X, int ldx, T* Xtmp, T* G, T* Ri, double shift_factor,
-                Scratch scr, int* info) {
+                Scratch scr, int* info, OzProd* oz) {
   cudaStream_t st = h->stream;
-  TRY(gemm<T>(st, true, l, l, n, X, ldx, X, ldx, G, l, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, scr,
-              true, false, &h->launches));
+  if (oz)
+    TRY(oz_gram<T>(h, *oz, l, X, ldx, X, ldx, G, l, scr));
+  else
+    TRY(gemm<T>(st, true, l, l, n, X, ldx, X, ldx, G, l, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, scr,
+                true, false, &h->launches));
   CHASE_CUDA_TRY(cudaMemsetAsync(&h->dstat->chol_info, 0, sizeof(int), st));
   if (l > 128)
     TRY(potrf_upper_blocked<T>(st, l, G, l, shift_factor, h->dstat, Ri, scr, &h->launches));
@@ -381,9 +488,15 @@ int cholqr_pass(chase_ctx* h, int n, int l, T* X, int ldx, T* Xtmp, T* G, T* Ri,
     TRY(potrf_upper<T>(st, l, G, l, shift_factor, h->dstat, &h->launches));
   CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h->hstat->timeout) return CHASE_ERR_TIMEOUT;
   *info = h->hstat->chol_info;
   if (*info) return CHASE_CHOL_FAILED;
   TRY(trtri_upper<T>(st, l, G, l, Ri, l, &h->launches));
+  if (oz) {
+    TRY(oz_prep_factor<T>(h, *oz, l, l, Ri, l));
+    TRY(oz_tall<T>(h, *oz, l, X, ldx, l, X, ldx, scr));
+    return 0;
+  }
   TRY(gemm<T>(st, false, n, l, l, X, ldx, Ri, l, Xtmp, n, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
               scr, false, true, &h->launches));
   TRY(copy_cols<T>(st, n, l, Xtmp, n, X, ldx, &h->launches));
@@ -395,7 +508,7 @@ int cholqr_pass(chase_ctx* h, int n, int l, T* X, int ldx, T* Xtmp, T* G, T* Ri,
 template <class T>
 int qr_dynamic(chase_ctx* h, int n, int l, T* X, int ldx, double log_est, double cond_hi,
                double cond_lo, int force, T* Xtmp, T* Xsave, T* G, T* Ri, Scratch scr,
-               int* variant_used, int* first_fail_info) {
+               int* variant_used, int* first_fail_info, OzProd* oz = nullptr) {
   cudaStream_t st = h->stream;
   int variant = force;
   if (force == 0) {
@@ -411,11 +524,11 @@ int qr_dynamic(chase_ctx* h, int n, int l, T* X, int ldx, double log_est, double
     int info = 0, rc = 0;
     if (variant == 1 || variant == 2) {
       for (int p = 0; p < variant && rc == 0; ++p)
-        rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, 0.0, scr, &info);
+        rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, 0.0, scr, &info, oz);
     } else if (variant == 3) {
-      rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, shift_factor, scr, &info);
+      rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, shift_factor, scr, &info, oz);
       for (int p = 0; p < 2 && rc == 0; ++p)
-        rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, 0.0, scr, &info);
+        rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, 0.0, scr, &info, oz);
     } else {
       TRY(householder_qr<T>(st, n, l, X, ldx, Xtmp, n, nullptr, &h->launches));
       break;
@@ -461,7 +574,8 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
   const bool mixed = (cfg.prec == CHASE_BF16X3);
   const bool emu = (cfg.prec == CHASE_BF16X3 || cfg.prec == CHASE_FP64_EMU);
   const size_t tcb_bytes = mixed ? tc_bytes<T>(n, l) : 0;
-  TRY(ensure_ws(h, L.total + tcb_bytes + (emu ? oz_bytes<T>(n, l) : 0)));
+  const size_t ozb_bytes = emu ? align256(oz_bytes<T>(n, l)) : 0;
+  TRY(ensure_ws(h, L.total + tcb_bytes + ozb_bytes + (emu ? ozp_bytes<T>(n, l) : 0)));
   TRY(ensure_hbuf(h, sizeof(double) * 4 * (size_t)l + 4096));
   char* base = (char*)h->ws;
   T* V = (T*)(base + L.V);
@@ -481,7 +595,12 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
   TcBufs tcb;
   if (mixed) tcb = tc_carve<T>(base + L.total, n, l);
   OzBufs ozb;
-  if (emu) ozb = oz_carve<T>(base + L.total + tcb_bytes, n, l);
+  OzProd ozp;
+  if (emu) {
+    ozb = oz_carve<T>(base + L.total + tcb_bytes, n, l);
+    ozp = ozp_carve<T>(base + L.total + tcb_bytes + ozb_bytes, n, l);
+  }
+  OzProd* ozq = emu ? &ozp : nullptr;
   bool lowprec = mixed, A_split = false, A_oz = false;
   const double normA_est = std::max(std::fabs(bd.lambda1), std::fabs(bd.b_sup));
   double* hw = h->hbuf;        // l Ritz values
@@ -525,7 +644,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     phase_begin();
     int v0 = 0, fi = 0;
     rc = qr_dynamic<T>(h, n, l, V, n, std::log(100.0), cfg.cond_hi, cfg.cond_lo,
-                       cfg.qr_force == 4 ? 4 : 0, P, Xs, G, Ri, scr, &v0, &fi);
+                       cfg.qr_force == 4 ? 4 : 0, P, Xs, G, Ri, scr, &v0, &fi, ozq);
     phase_end(S.t_qr);
   }
 
@@ -571,7 +690,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     if (k > 0) rc = copy_cols<T>(st, n, k, V, n, T2, n, &h->launches);
     int variant = 0, fi = 0;
     if (!rc) rc = qr_dynamic<T>(h, n, l, V, n, lest, cfg.cond_hi, cfg.cond_lo, cfg.qr_force, P, Xs,
-                                G, Ri, scr, &variant, &fi);
+                                G, Ri, scr, &variant, &fi, ozq);
     if (!rc && k > 0) rc = copy_cols<T>(st, n, k, T2, n, V, n, &h->launches);
     phase_end(S.t_qr);
     if (rc) break;
@@ -591,8 +710,13 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       rc = gemm<T>(st, false, n, nu, n, A, lda, Q2, n, AQ, n, 1.0, 0.0, nullptr, 0, 0.0, nullptr,
                    0, scr, false, false, &h->launches);
     }
-    if (!rc) rc = gemm<T>(st, true, nu, nu, n, Q2, n, AQ, n, H, nu, 1.0, 0.0, nullptr, 0, 0.0,
-                          nullptr, 0, scr, true, false, &h->launches);
+    if (rc) {
+    } else if (ozq) {
+      rc = oz_gram<T>(h, ozp, nu, Q2, n, AQ, n, H, nu, scr);
+    } else {
+      rc = gemm<T>(st, true, nu, nu, n, Q2, n, AQ, n, H, nu, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
+                   scr, true, false, &h->launches);
+    }
     if (!rc) rc = herm_fill_lower<T>(st, nu, H, nu, &h->launches);
     int sweeps = 0;
     cudaEvent_t j0, j1;
@@ -606,21 +730,30 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     S.jacobi_sweeps += sweeps;
     cudaEventDestroy(j0);
     cudaEventDestroy(j1);
-    // V <- Q2 W (via T2), AV = AQ W (into P)
-    if (!rc) rc = gemm<T>(st, false, n, nu, nu, Q2, n, Wm, nu, T2, n, 1.0, 0.0, nullptr, 0, 0.0,
-                          nullptr, 0, scr, false, false, &h->launches);
-    if (!rc) rc = gemm<T>(st, false, n, nu, nu, AQ, n, Wm, nu, P, n, 1.0, 0.0, nullptr, 0, 0.0,
-                          nullptr, 0, scr, false, false, &h->launches);
-    if (!rc) rc = copy_cols<T>(st, n, nu, T2, n, Q2, n, &h->launches);
+    // V <- Q2 W, AV = AQ W (into P)
+    if (rc) {
+    } else if (ozq) {
+      rc = oz_prep_factor<T>(h, ozp, nu, nu, Wm, nu);
+      if (!rc) rc = oz_tall<T>(h, ozp, nu, AQ, n, nu, P, n, scr);
+      if (!rc) rc = oz_tall<T>(h, ozp, nu, Q2, n, nu, Q2, n, scr);
+    } else {
+      rc = gemm<T>(st, false, n, nu, nu, Q2, n, Wm, nu, T2, n, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
+                   scr, false, false, &h->launches);
+      if (!rc) rc = gemm<T>(st, false, n, nu, nu, AQ, n, Wm, nu, P, n, 1.0, 0.0, nullptr, 0, 0.0,
+                            nullptr, 0, scr, false, false, &h->launches);
+      if (!rc) rc = copy_cols<T>(st, n, nu, T2, n, Q2, n, &h->launches);
+    }
     phase_end(S.t_rr);
     if (rc) break;
     // --- residuals (eq. res) ---
     phase_begin();
     rc = resid_norms<T>(st, n, nu, P, n, Q2, n, dw, dres, &h->launches);
     if (!rc) rc = (cudaMemcpyAsync(hw, dw, sizeof(double) * nu, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-                   cudaMemcpyAsync(hr, dres, sizeof(double) * nu, cudaMemcpyDeviceToHost, st) == cudaSuccess)
+                   cudaMemcpyAsync(hr, dres, sizeof(double) * nu, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                   cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st) == cudaSuccess)
                       ? 0 : CHASE_ERR_CUDA;
     phase_end(S.t_resid);
+    if (!rc && h->hstat->timeout) rc = CHASE_ERR_TIMEOUT;
     if (rc) break;
     for (int a = 0; a < nu; ++a) {
       ritz[k + a] = hw[a];
@@ -762,12 +895,14 @@ int filter_impl(chase_ctx* h, int n, const T* A, int lda, int ncols, const T* dV
 }
 
 template <class T>
-int qr_impl(chase_ctx* h, int n, int l, T* X, int ldx, double est, int force, int* variant_used,
-            int* chol_info) {
+int qr_impl(chase_ctx* h, int n, int l, T* X, int ldx, double est, int force, chase_precision prec,
+            int* variant_used, int* chol_info) {
   cudaStream_t st = h->stream;
   const size_t blk = align256(sizeof(T) * (size_t)n * l);
   const size_t sq = align256(sizeof(T) * (size_t)l * l);
-  TRY(ensure_ws(h, 2 * blk + 2 * sq + kScratchBytes));
+  const bool emu = (prec == CHASE_FP64_EMU || prec == CHASE_BF16X3);
+  const size_t fixed = 2 * blk + 2 * sq + kScratchBytes;
+  TRY(ensure_ws(h, fixed + (emu ? ozp_bytes<T>(n, l) : 0)));
   char* base = (char*)h->ws;
   T* Xtmp = (T*)base;
   T* Xsave = (T*)(base + blk);
@@ -777,7 +912,10 @@ int qr_impl(chase_ctx* h, int n, int l, T* X, int ldx, double est, int force, in
   double lest = (est > 0.0) ? std::log(est) : -1e300;
   if (!std::isfinite(est) && est > 0) lest = 1e300;
   int v = 0, fi = 0;
-  int rc = qr_dynamic<T>(h, n, l, X, ldx, lest, 1e8, 20.0, force, Xtmp, Xsave, G, Ri, scr, &v, &fi);
+  OzProd ozp;
+  if (emu) ozp = ozp_carve<T>(base + fixed, n, l);
+  int rc = qr_dynamic<T>(h, n, l, X, ldx, lest, 1e8, 20.0, force, Xtmp, Xsave, G, Ri, scr, &v, &fi,
+                         emu ? &ozp : nullptr);
   if (variant_used) *variant_used = v;
   if (chol_info) *chol_info = fi;
   if (rc && rc != CHASE_CHOL_FAILED) return rc;
@@ -882,7 +1020,9 @@ int chase_workspace_bytes(chase_dtype dtype, int n, int nev, int nex, chase_prec
   size_t b = (dtype == CHASE_R64) ? layout_for<double>(n, l).total : layout_for<z64>(n, l).total;
   if (prec == CHASE_BF16X3) b += (dtype == CHASE_R64) ? tc_bytes<double>(n, l) : tc_bytes<z64>(n, l);
   if (prec == CHASE_BF16X3 || prec == CHASE_FP64_EMU)
-    b += (dtype == CHASE_R64) ? oz_bytes<double>(n, l) : oz_bytes<z64>(n, l);
+    b += (dtype == CHASE_R64)
+             ? align256(oz_bytes<double>(n, l)) + ozp_bytes<double>(n, l)
+             : align256(oz_bytes<z64>(n, l)) + ozp_bytes<z64>(n, l);
   *bytes = b;
   return CHASE_OK;
 }
@@ -968,8 +1108,9 @@ int chase_filter(chase_handle h, chase_dtype dtype, int n, const void* dA, int l
                           lambda1, prec, (z64*)dVout, ldvout);
 }
 
-int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int ldx,
-             double est_cond, int qr_force, int* variant_used, int* chol_info) {
+int chase_qr_prec(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int ldx,
+                  double est_cond, int qr_force, chase_precision prec, int* variant_used,
+                  int* chol_info) {
   if (!h) return -1;
   if (dtype != CHASE_R64 && dtype != CHASE_C128) return -2;
   if (n < 1) return -3;
@@ -978,10 +1119,18 @@ int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int 
   if (ldx < n) return -6;
   if (std::isnan(est_cond)) return -7;
   if (qr_force < 0 || qr_force > 4) return -8;
+  if (prec != CHASE_FP64 && prec != CHASE_FP64_EMU) return -9;
   if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
   if (dtype == CHASE_R64)
-    return qr_impl<double>(h, n, ncols, (double*)dX, ldx, est_cond, qr_force, variant_used, chol_info);
-  return qr_impl<z64>(h, n, ncols, (z64*)dX, ldx, est_cond, qr_force, variant_used, chol_info);
+    return qr_impl<double>(h, n, ncols, (double*)dX, ldx, est_cond, qr_force, prec, variant_used,
+                           chol_info);
+  return qr_impl<z64>(h, n, ncols, (z64*)dX, ldx, est_cond, qr_force, prec, variant_used, chol_info);
+}
+
+int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int ldx,
+             double est_cond, int qr_force, int* variant_used, int* chol_info) {
+  return chase_qr_prec(h, dtype, n, ncols, dX, ldx, est_cond, qr_force, CHASE_FP64, variant_used,
+                       chol_info);
 }
 
 int chase_lanczos_bounds(chase_handle h, chase_dtype dtype, int n, const void* dA, int lda,

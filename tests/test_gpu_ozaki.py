@@ -101,3 +101,60 @@ def test_solve_with_emulated_fp64_matches_oracle(cl, handle, prec_name):
     if prec_name == "CHASE_FP64_EMU":
         assert abs(st["iterations"] - ref["summary"]["iterations"]) <= 1
         assert abs(st["matvecs"] - ref["summary"]["matvecs"]) <= 0.05 * ref["summary"]["matvecs"]
+
+
+# --------------------------------------------------------------------------
+# QR with emulated-FP64 block products (Gram X^H X and X R^{-1}, Algorithm 2)
+# --------------------------------------------------------------------------
+
+def _unitary(n, seed, complex_):
+    Q, R = np.linalg.qr(W.gaussian((n, n), seed, complex_))
+    return Q * (np.diag(R) / np.abs(np.diag(R)))
+
+
+def _sv_matrix(n, l, sv, seed, complex_):
+    return (_unitary(n, seed, complex_)[:, :l] * sv) @ _unitary(l, seed + 1, complex_).conj().T
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+@pytest.mark.parametrize("n,l,force,log10k", [
+    (421, 37, 1, 0), (421, 37, 2, 4), (421, 37, 3, 10),
+    (1500, 150, 2, 2),     # several tiles each way, split-K over the long dimension
+    (2100, 200, 3, 8),
+])
+def test_qr_with_emulated_products_matches_oracle(cl, handle, complex_, n, l, force, log10k):
+    """Q against the oracle (unique factor with positive diagonal R) to the FP64 parity
+    tolerance, orthogonality to 1e-12 (1e-10 for CholQR1), X = Q R with R upper."""
+    X = _sv_matrix(n, l, np.logspace(0, -log10k, l), 500 + n + log10k, complex_)
+    Qo, vo, io = oracle.qr_dynamic(X, 0.0, force=force)
+    Xd = dev(X)
+    rc, v, info = cl.chase_qr(handle, Xd, 1.0, qr_force=force, prec=cl.CHASE_FP64_EMU)
+    Q = Xd.cpu().numpy()
+    assert rc == 0 and v == force and io == 0 and info == 0
+    orth = np.linalg.norm(Q.conj().T @ Q - np.eye(l))
+    assert orth <= (1e-10 if force == 1 else 1e-12)
+    if 10.0 ** log10k <= 1e4:
+        assert np.abs(Q - Qo).max() <= 1e-9
+    R = Q.conj().T @ X
+    assert np.linalg.norm(np.tril(R, -1)) <= 1e-10 * np.linalg.norm(X)
+
+
+def test_qr_emulated_escalates_like_fp64(cl, handle):
+    """kappa ~ 1e15: a CholQR2 chosen by a too-small estimate fails and escalates; the
+    result is orthonormal; a forced CholQR2 reports the failure with X unchanged."""
+    X = _sv_matrix(300, 20, np.logspace(0, -15, 20), 78, True)
+    Xd = dev(X)
+    rc, v, info = cl.chase_qr(handle, Xd, 100.0, prec=cl.CHASE_FP64_EMU)
+    assert rc == 0 and v in (3, 4) and info != 0
+    Q = Xd.cpu().numpy()
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(20)) <= 1e-11
+    Xd = dev(X)
+    rc, v, info = cl.chase_qr(handle, Xd, 1.0, qr_force=2, prec=cl.CHASE_FP64_EMU)
+    assert rc == cl.CHASE_CHOL_FAILED and info > 0
+    np.testing.assert_array_equal(Xd.cpu().numpy(), X)
+
+
+def test_qr_prec_rejects_other_precisions(cl, handle):
+    Xd = dev(W.gaussian((50, 5), 1, False))
+    rc, v, info = cl.chase_qr(handle, Xd, 1.0, prec=cl.CHASE_TF32, check=False)
+    assert rc == -9
