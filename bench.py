@@ -37,6 +37,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Dense BF16 tensor peak measured on the GB300s (cuBLAS, burst), MEASURED_PEAKS.json.
 BF16_PEAK_TFLOPS = 1978.3
 BF16_SUSTAINED_TFLOPS = 1717.0
+# BF16 digit products per real FP64 product in the Ozaki-scheme kernel: 7 digits per operand,
+# pairs (i, j) with i + j <= 8.
+OZAKI_PAIRS = 28
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
@@ -123,8 +126,8 @@ def run_filter(args):
         line["frac_of_fp64_peak"] = flops / t / 1e12 / FP64_PEAK_TFLOPS
     else:
         # BF16 tensor-core products of the stacked real operator (2n x 2n) per step:
-        # 3 for BF16x3, 36 slice pairs for the Ozaki scheme
-        npairs = 3 if args.prec == "bf16x3" else 36
+        # 3 for BF16x3, OZAKI_PAIRS digit pairs for the Ozaki scheme
+        npairs = 3 if args.prec == "bf16x3" else OZAKI_PAIRS
         tc = npairs * 2.0 * (2 * n) * (2 * n) * k * args.degree / t / 1e12
         line["bf16_tensor_tflops"] = tc
         line["frac_of_bf16_peak"] = tc / BF16_PEAK_TFLOPS
@@ -531,10 +534,10 @@ def main():
     eval_err = max(float(np.abs(r[1] - lam).max()) for r in results)
     rc, ev, res, st, logs = results[-1]
     launches = sum(r[3]["kernel_launches"] for r in results)
-    # roofline of the dominant kernel: the filter product (CUDA-event time of the filter phase,
-    # which is almost all product launches, divided by the launch count)
+    # roofline of the dominant kernel: the filter product (CUDA events around each product
+    # launch on the handle's stream, summed by the library, divided by the launch count)
     nl = max(1, st["filter_launches"])
-    dur_launch = st["t_filter"] / nl
+    dur_launch = st["t_filter_product"] / nl
     if args.prec == "fp64":
         fl_launch = st["filter_flops"] / nl
         achieved = fl_launch / dur_launch / 1e12 if dur_launch > 0 else None
@@ -543,10 +546,10 @@ def main():
                 "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz", "traffic": None}
     else:
-        # BF16 tensor work: 36 slice products per FP64-equivalent flop pair for the Ozaki
+        # BF16 tensor work: OZAKI_PAIRS digit products per FP64-equivalent flop for the Ozaki
         # product, 3 for the BF16x3 filter iterations
         lp = st["filter_flops_lowprec"]
-        tc_flops = 36.0 * (st["filter_flops"] - lp) + 3.0 * lp
+        tc_flops = OZAKI_PAIRS * (st["filter_flops"] - lp) + 3.0 * lp
         achieved = tc_flops / nl / dur_launch / 1e12 if dur_launch > 0 else None
         roof = {"kernel": "oz_gemm_kernel (Ozaki-scheme FP64 product on BF16 tcgen05)" +
                           (" + tc_filter_bf16x3_kernel" if lp > 0 else ""),
@@ -605,7 +608,10 @@ def main():
         h2d = A_h.numel() * A_h.element_size() + V0_h.numel() * V0_h.element_size()
         d2h = Y_h.numel() * Y_h.element_size() + 2 * 8 * prob.nev
         line["e2e"] = {"value": world * args.steps / t_e2e, "unit": "solves/s",
-                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "converged": bool(rc2 == 0 and float(res2.max()) < prob.tol),
+                       "iterations": st2["iterations"],
+                       "max_abs_eval_err_vs_known": float(np.abs(ev2 - lam).max())}
         del A_d, V_d
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         A_host = A.cpu().numpy()

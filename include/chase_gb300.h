@@ -121,6 +121,8 @@ typedef struct {
   double filter_flops_lowprec; /* their algorithmic flops (counted as for FP64) */
   double t_rr_eig;         /* part of t_rr spent in the Jacobi eigensolver */
   int jacobi_sweeps;       /* Jacobi sweeps summed over iterations */
+  double t_filter_product; /* part of t_filter spent in the product kernels alone (CUDA events
+                              around each launch) */
 } chase_stats;
 
 /* Per-iteration record (the kind of data Figure 2 plots). */

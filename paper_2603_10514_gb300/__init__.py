@@ -65,7 +65,7 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int), ("filter_launches", ctypes.c_int),
                 ("n_lowprec_iters", ctypes.c_int), ("t_filter_lowprec", ctypes.c_double),
                 ("filter_flops_lowprec", ctypes.c_double), ("t_rr_eig", ctypes.c_double),
-                ("jacobi_sweeps", ctypes.c_int)]
+                ("jacobi_sweeps", ctypes.c_int), ("t_filter_product", ctypes.c_double)]
 
 
 class IterLog(ctypes.Structure):

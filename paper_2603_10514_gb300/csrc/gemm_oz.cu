@@ -1,39 +1,54 @@
 // gemm_oz.cu -- FP64-accurate dense products on the BF16 tensor cores by the
 // Ozaki scheme (Ozaki, Ogita, Oishi & Rump, "Error-free transformations of
 // matrix multiplication by using fast routines of matrix multiplication and its
-// applications", Numer. Algorithms 2012), for the filter's A*V and the
-// Rayleigh-Ritz product A*Q.
+// applications", Numer. Algorithms 2012): the filter's A*V, the Rayleigh-Ritz
+// product A*Q and the block products of the QR and Rayleigh-Ritz steps.
 //
-// Slicing.  Every row m of the (stacked real) A is scaled by 2^-e_m so that its
-// entries lie in (-1, 1), every column c of V by 2^-f_c, and each scaled entry
-// is cut into S = 8 signed digits by rounding to nearest: x = sum_i d_i 2^{-7i}
-// + O(2^-57), |d_1| <= 128, |d_i| <= 64 (i > 1).  Digits are exact in BF16.  Then
-//   (A V)[m, c] = 2^{e_m + f_c} sum_{t=2}^{9} 2^{-7t} L_t[m, c],
-//   L_t = sum_{i + j = t} A_i V_j        (pairs with i + j > 9 are dropped:
-//                                         their weight is below 2^-63),
-// 36 BF16 products per output.  Levels 2..5 carry the leading bits and must
-// be summed exactly: each is an integer whose partial sum over a K chunk of
-// 256 is bounded by 256 * (2 * 128 * 64 + 2 * 64 * 64) < 2^23 (level 5, the
-// largest), so every partial sum is an integer FP32 represents and the tensor
-// core's FP32 accumulation is exact; after every chunk the epilogue adds them, shifted
-// into place, into one int64 per output, which stays exact over the whole K.
-// Levels 6..9 weigh at most 2^-28 of level 2, so FP32 accumulation over the
-// whole K (relative rounding 2^-24) keeps their error below 2^-52 of the
-// result; they are read once at the end.  The result is A*V to within
-// ~2^-53 K max|A_m.| max|V_.c| per entry, the accuracy class of an FP64 GEMM.
+// Slicing.  Every row m of the (stacked real) left operand is scaled by 2^-e_m
+// so that its entries lie in (-1, 1), every column c of the right operand by
+// 2^-f_c, and each scaled entry is cut into S = 7 signed 8-bit digits by
+// rounding to nearest: x = sum_i d_i 2^{-8i} + O(2^-57), |d_1| <= 256,
+// |d_i| <= 128 (i > 1).  Then
+//   (A V)[m, c] = 2^{e_m + f_c} sum_{t=2}^{8} 2^{-8t} L_t[m, c],
+//   L_t = sum_{i + j = t} A_i V_j        (pairs with i + j > 8 are dropped:
+//                                         their weight is below 2^-56),
+// 28 BF16 products per output.  Digit i is stored pre-scaled as
+// d_i 2^{-8(i-3)} (exact in BF16: an integer of at most 8 significant bits
+// times a power of two), so that every pair of level t contributes
+// d_i d_j 2^{-8(t-6)}: one scale per level on both operands.
+//   * Levels 2..5 carry the leading bits and are summed exactly: the integer
+//     L_t over a K chunk of 128 is below 128 (2^16 + 2^15) < 2^24 (level 5, the
+//     largest), so the tensor core's FP32 accumulation of the scaled integers is
+//     exact; after every chunk the epilogue converts them (32-bit conversions),
+//     shifts them into place and adds them into one int64 per output, which
+//     stays exact over the whole K.
+//   * Levels 6..8 weigh at most 2^-32 of level 2; each has its own FP32
+//     accumulator over the whole K, read once at the end.  One shared
+//     accumulator for all three does not work: measured on GB300, adding the
+//     small levels into the larger running sum loses their low bits with a
+//     bias (the accumulation truncates), and the error grew linearly in K to
+//     ~1e-11 relative at K = 8192; with one accumulator per level it is 5e-15.
+// The result is A*V to within ~2^-53 K max|A_m.| max|V_.c| per entry, the
+// accuracy class of an FP64 GEMM.
 //
 // Kernel: one CTA per 128 x 64 output tile, 320 threads:
-//   warp 0     TMA producer: per 64-wide K block, the 8 V digit tiles
-//              (64 x 64 BF16, one "V stage", 2 stages) and the 8 A digit
-//              tiles (128 x 64 BF16) streamed through a 4-deep ring;
-//   warp 1     allocates all 512 TMEM columns (8 levels x 64) and issues the
-//              tcgen05.mma.kind::f16 (M 128, N 64, K 16): 144 per K block;
-//   warps 2-9  epilogue: per 256-wide chunk, tcgen05.ld of levels 2..5 for 32
-//              rows x 32 columns and exact int64 accumulation; at the end
-//              levels 6..9, the FP64 recombination and the Chebyshev
+//   warp 0     TMA producer: per 32-wide K block one stage holding the 7 A digit
+//              tiles (128 x 32 BF16) and the 7 V digit tiles (64 x 32), two
+//              stages (84 KB each, 64-byte swizzle);
+//   warp 1     allocates 512 TMEM columns (7 level accumulators x 64) and issues
+//              the tcgen05.mma.kind::f16 (M 128, N 64, K 16): 56 per K block.
+//              The exact levels are issued before the tail levels in the last
+//              block of a chunk and after them in the first, so the epilogue
+//              reads a finished chunk while the tensor core works on the tail;
+//   warps 2-9  epilogue: 4 lane quarters x 2 column halves; per chunk a
+//              tcgen05.ld of levels 2..5 and exact int64 accumulation; at the
+//              end levels 6..8, the FP64 recombination and the Chebyshev
 //              three-term update.
+// Digit slicing is integer arithmetic on the FP64 bit patterns (FP64 issues at
+// 2 per clock per SM on this part; the integer pipes at 64).
 // All mbarrier waits are bounded; on expiry the kernel records the failure in
-// the device status word, frees its TMEM and returns.
+// the device status word, waits (bounded) for its copies and MMAs in flight,
+// frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -47,18 +62,24 @@ namespace chase {
 
 namespace {
 
-constexpr int OZ_S = 8;          // digits per entry
-constexpr int OZ_B = 7;          // bits per digit
-constexpr int OZ_LEVELS = 8;     // t = 2 .. 9
-constexpr int OBM = 128, OBN = 64, OBK = 64;
-constexpr int OZ_CHUNK_KB = 4;   // 4 K blocks = 256 K per exact chunk (levels 2..5)
-constexpr int OA_RING = 4;
-constexpr int A_TILE = OBM * OBK * 2;          // 16 KB
-constexpr int V_TILE = OBN * OBK * 2;          // 8 KB
-constexpr int V_STAGE = OZ_S * V_TILE;         // 64 KB
-constexpr int OZ_THREADS = 320;
-constexpr int OZ_SMEM = 2 * V_STAGE + OA_RING * A_TILE + 1024 + 512;
+constexpr int OZ_S = 7;          // digits per entry
+constexpr int OZ_B = 8;          // bits per digit
+constexpr int OZ_T0 = 6;         // first tail level; digit i is stored as d_i 2^{-8(i - 3)}
+constexpr int OZ_NACC = OZ_S;    // one accumulator per level t = 2..8
+constexpr int OBM = 128, OBN = 64, OBK = 32;
+constexpr int OZ_CHUNK_KB = 4;   // 4 K blocks = 128 K per exact chunk
+constexpr int A_TILE = OBM * OBK * 2;           // 8 KB
+constexpr int V_TILE = OBN * OBK * 2;           // 4 KB
+constexpr int STAGE = OZ_S * (A_TILE + V_TILE); // 84 KB
+constexpr int NSTAGE = 2;
+constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
+constexpr int OZ_SMEM = NSTAGE * STAGE + 1024 + 256;
 constexpr long long kOzWait = 4000000000LL;
+static_assert(OZ_NACC * OBN <= 512, "accumulators exceed TMEM");
+static_assert(STAGE % 1024 == 0 && A_TILE % 512 == 0 && V_TILE % 512 == 0, "tile alignment");
+static_assert(OZ_SMEM <= 232448, "shared memory");
+static_assert(kOzPlaneBytes == 2 * OZ_S, "workspace plane size");
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -98,9 +119,11 @@ __device__ __forceinline__ void tma3(void* dst, const CUtensorMap* m, uint64_t* 
       "l"((uint64_t)m), "r"(s32(b)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t a) {
-  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// Shared-memory matrix descriptor, K-major, 64-byte swizzle: rows of 64 bytes (32 BF16
+// of K), 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t a) {
+  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OBN >> 3) << 17) |
                             ((uint32_t)(OBM >> 4) << 24);
@@ -128,6 +151,41 @@ __device__ __forceinline__ void ld32(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// MMAs of one K block for the pairs of the exact levels (t = 2..5) or of the tail
+// (t = 6..8), in level order; each pair is 2 K-steps of 16.  restart: the first MMA into
+// each accumulator overwrites it (exact: at a chunk start; tail: at the first block).
+template <bool kTail>
+__device__ __forceinline__ void issue_pairs(uint32_t tmem, uint64_t da0, uint64_t dv0, bool restart) {
+#pragma unroll
+  for (int t = kTail ? OZ_T0 : 2; t <= (kTail ? OZ_S + 1 : OZ_T0 - 1); ++t) {
+#pragma unroll
+    for (int i = 1; i <= OZ_S; ++i) {
+      const int j = t - i;
+      if (j < 1 || j > OZ_S) continue;
+      const uint32_t acc_col = (uint32_t)((t - 2) * OBN);
+      const bool first = (i == 1);
+      const uint64_t da = da0 + (uint64_t)(((i - 1) * A_TILE) >> 4);
+      const uint64_t dv = dv0 + (uint64_t)(((j - 1) * V_TILE) >> 4);
+#pragma unroll
+      for (int kk = 0; kk < OBK / 16; ++kk) {
+        const uint64_t off = (uint64_t)((kk * 32) >> 4);
+        mma(tmem + acc_col, da + off, dv + off, (first && kk == 0 && restart) ? 0u : 1u);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
                    int M, int N, int nkb_total, int kbs, int col0, const int* __restrict__ rowexp,
@@ -136,16 +194,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                    double* __restrict__ partial, DevStatus* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* vst = smem;                          // 2 V stages
-  unsigned char* ast = smem + 2 * V_STAGE;            // A ring
-  uint64_t* bars = (uint64_t*)(ast + OA_RING * A_TILE);
-  uint64_t* vfull = bars;                             // [2]
-  uint64_t* vempty = bars + 2;                        // [2]
-  uint64_t* afull = bars + 4;                         // [4]
-  uint64_t* aempty = bars + 8;                        // [4]
-  uint64_t* cfull = bars + 12;                        // chunk accumulated in TMEM
-  uint64_t* cfree = bars + 13;                        // chunk read out of TMEM
-  uint32_t* tslot = (uint32_t*)(bars + 14);
+  uint64_t* bars = (uint64_t*)(smem + NSTAGE * STAGE);
+  uint64_t* full = bars;                              // [2] stage loaded
+  uint64_t* empty = bars + 2;                         // [2] stage consumed by the MMAs
+  uint64_t* cfull = bars + 4;                         // exact levels of a chunk accumulated
+  uint64_t* cfree = bars + 5;                         // exact levels read out of TMEM
+  uint64_t* tdone = bars + 6;                         // every MMA of the CTA finished
+  uint32_t* tslot = (uint32_t*)(bars + 7);
   int* s_err = (int*)(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -156,10 +211,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int nchunks = (nkb + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) { bar_init(&vfull[i], 1); bar_init(&vempty[i], 1); }
-    for (int i = 0; i < OA_RING; ++i) { bar_init(&afull[i], 1); bar_init(&aempty[i], 1); }
+    for (int i = 0; i < NSTAGE; ++i) { bar_init(&full[i], 1); bar_init(&empty[i], 1); }
     bar_init(cfull, 1);
-    bar_init(cfree, 8);  // one arrival per epilogue warp
+    bar_init(cfree, OZ_EPI_WARPS);  // one arrival per epilogue warp
+    bar_init(tdone, 1);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -176,123 +231,126 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- producer ----------------
-    int ai = 0;
+    int issued = 0;
     for (int kb = 0; kb < nkb && !*(volatile int*)s_err; ++kb) {
-      const int vs = kb & 1;
-      const uint32_t vph = (uint32_t)((kb >> 1) & 1);
-      if (!bar_wait(&vempty[vs], vph ^ 1)) { atomicOr(s_err, 1); break; }
-      bar_expect(&vfull[vs], V_STAGE);
-      for (int j = 0; j < OZ_S; ++j)
-        tma3(vst + vs * V_STAGE + j * V_TILE, &mapV, &vfull[vs], (kbeg + kb) * OBK, col0 + n0, j);
-      for (int i = 0; i < OZ_S; ++i, ++ai) {
-        const int as = ai % OA_RING;
-        const uint32_t aph = (uint32_t)((ai / OA_RING) & 1);
-        if (!bar_wait(&aempty[as], aph ^ 1)) { atomicOr(s_err, 1); break; }
-        bar_expect(&afull[as], A_TILE);
-        tma3(ast + as * A_TILE, &mapA, &afull[as], (kbeg + kb) * OBK, m0, i);
-      }
+      const int s = kb & 1;
+      if (!bar_wait(&empty[s], (uint32_t)(((kb >> 1) & 1) ^ 1))) { atomicOr(s_err, 1); break; }
+      bar_expect(&full[s], STAGE);
+      unsigned char* st = smem + s * STAGE;
+      const int x = (kbeg + kb) * OBK;
+      for (int i = 0; i < OZ_S; ++i) tma3(st + i * A_TILE, &mapA, &full[s], x, m0, i);
+      for (int j = 0; j < OZ_S; ++j) tma3(st + OZ_S * A_TILE + j * V_TILE, &mapV, &full[s], x, col0 + n0, j);
+      issued = kb + 1;
     }
+    // copies still in flight land before the CTA can exit (already done on the normal path)
+    for (int b = max(0, issued - NSTAGE); b < issued; ++b)
+      if (!bar_wait(&full[b & 1], (uint32_t)((b >> 1) & 1))) atomicOr(s_err, 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    // Fully unrolled: pair (i, j), level t = i + j, 4 K-steps of 16 per pair; the only
-    // runtime inputs per MMA are the chunk-start / first-block flags.
-    int ai = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
+    bool bad = false;
+    for (int kb = 0; kb < nkb && !bad; ++kb) {
       const int chunk = kb / OZ_CHUNK_KB;
       const bool chunk_start = (kb % OZ_CHUNK_KB) == 0;
-      const bool first_kb = kb == 0;
-      if (chunk_start && chunk > 0) {
-        if (!bar_wait(cfree, (uint32_t)((chunk - 1) & 1))) { atomicOr(s_err, 2); break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      }
-      const int vs = kb & 1;
-      if (!bar_wait(&vfull[vs], (uint32_t)((kb >> 1) & 1))) { atomicOr(s_err, 2); break; }
+      const bool chunk_last = (kb % OZ_CHUNK_KB) == OZ_CHUNK_KB - 1 || kb == nkb - 1;
+      const int s = kb & 1;
+      if (!bar_wait(&full[s], (uint32_t)((kb >> 1) & 1))) { bad = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t dv0 = desc_sw128(s32(vst + vs * V_STAGE));
-      bool bad = false;
-#pragma unroll
-      for (int i = 1; i <= OZ_S; ++i) {
-        const int as = ai % OA_RING;
-        if (!bar_wait(&afull[as], (uint32_t)((ai / OA_RING) & 1))) { bad = true; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t da = desc_sw128(s32(ast + as * A_TILE));
-#pragma unroll
-        for (int j = 1; j <= OZ_S + 1 - i; ++j) {
-          const int t = i + j;
-          const uint32_t dcol = tmem + (uint32_t)((t - 2) * OBN);
-          const uint64_t dv = dv0 + (uint64_t)(((j - 1) * V_TILE) >> 4);
-          const bool restart_flag = (t <= 5) ? chunk_start : first_kb;
-#pragma unroll
-          for (int kk = 0; kk < OBK / 16; ++kk) {
-            const uint64_t off = (uint64_t)((kk * 32) >> 4);
-            const uint32_t acc = (i == 1 && kk == 0 && restart_flag) ? 0u : 1u;
-            mma(dcol, da + off, dv + off, acc);
-          }
+      const uint32_t sa = s32(smem + s * STAGE);
+      const uint64_t da0 = desc_sw64(sa), dv0 = desc_sw64(sa + OZ_S * A_TILE);
+      if (chunk_start) {
+        // tail first: the epilogue may still be reading the previous chunk's exact levels
+        issue_pairs<true>(tmem, da0, dv0, kb == 0);
+        if (chunk > 0) {
+          if (!bar_wait(cfree, (uint32_t)((chunk - 1) & 1))) { bad = true; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        commit(&aempty[as]);
-        ++ai;
+        issue_pairs<false>(tmem, da0, dv0, true);
+        if (chunk_last) commit(cfull);
+      } else {
+        issue_pairs<false>(tmem, da0, dv0, false);
+        if (chunk_last) commit(cfull);
+        issue_pairs<true>(tmem, da0, dv0, false);
       }
-      if (bad) { atomicOr(s_err, 2); break; }
-      commit(&vempty[vs]);
-      if ((kb % OZ_CHUNK_KB) == OZ_CHUNK_KB - 1 || kb == nkb - 1) commit(cfull);
+      commit(&empty[s]);
     }
+    if (bad) atomicOr(s_err, 2);
+    commit(tdone);  // arrives once every MMA issued above has completed
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int q = warp & 3;            // TMEM lane quarter this warp may access
-    const int hc = (warp - 2) >> 2;    // column half of the 64-wide tile
-    const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(hc * 32);
+    const int q = warp & 3;             // TMEM lane quarter this warp may access
+    const int cg = (warp - 2) >> 2;     // column group of 32
+    const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cg * 32);
     long long g1[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) g1[j] = 0;
     bool ok = true;
+    // waits are taken by every lane and made warp-uniform: the tcgen05.ld below are
+    // .sync.aligned and must be executed by the whole warp or not at all
     for (int c = 0; c < nchunks && ok; ++c) {
-      if (!bar_wait(cfull, (uint32_t)(c & 1))) { ok = false; atomicOr(s_err, 4); break; }
+      if (!__all_sync(0xffffffffu, bar_wait(cfull, (uint32_t)(c & 1)))) {
+        ok = false;
+        if (lane == 0) atomicOr(s_err, 4);
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-      for (int t = 2; t <= 5; ++t) {
+      for (int t = 2; t < OZ_T0; ++t) {
         uint32_t r[32];
         ld32(tbase + (uint32_t)((t - 2) * OBN), r);
-        const long long sh = 1LL << (OZ_B * (5 - t));
+        // accumulator = L_t 2^{8(6 - t)} with |L_t| < 2^24: a 32-bit conversion recovers L_t
+        // exactly; G1 counts in units of level 5, L_t 2^{8(5 - t)}
+        const float unscale = __int_as_float((127 - OZ_B * (OZ_T0 - t)) << 23);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) g1[j] += (long long)__float2int_rz(__uint_as_float(r[j])) * sh;
+        for (int j = 0; j < 32; ++j)
+          g1[j] += (long long)__float2int_rz(__uint_as_float(r[j]) * unscale) << (OZ_B * (OZ_T0 - 1 - t));
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0 && c + 1 < nchunks) bar_arrive(cfree);
     }
+    if (ok && nkb > 0 && !__all_sync(0xffffffffu, bar_wait(tdone, 0u))) {
+      ok = false;
+      if (lane == 0) atomicOr(s_err, 4);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int r = m0 + 32 * q + lane;
     if (nkb == 0) ok = true;  // empty split: contributes zeros
-    if (ok && !*(volatile int*)s_err) {
-      // levels 6..9 (FP32 over the whole K), combined with level sum 2..5 in FP64
-      double y[32];
+    if (__shfl_sync(0xffffffffu, (int)(ok && !*(volatile int*)s_err), 0)) {
+      const int er = (r < M) ? rowexp[r] : 0;
+      // two halves of 16 columns keep g1 and the tail levels in registers
 #pragma unroll
-      for (int j = 0; j < 32; ++j) y[j] = 0.0;
+      for (int h = 0; h < 2; ++h) {
+        double y[16];  // tail levels, summed smallest first, in units of level 5 times 2^8
+#pragma unroll
+        for (int j = 0; j < 16; ++j) y[j] = 0.0;
+        if (nkb > 0) {
 #pragma unroll 1
-      for (int t = 9; t >= 6 && nkb > 0; --t) {
-        uint32_t rr[32];
-        ld32(tbase + (uint32_t)((t - 2) * OBN), rr);
-        const double w = ldexp(1.0, -OZ_B * (t - 5));  // relative to the 2..5 sum's unit
+          for (int t = OZ_S + 1; t >= OZ_T0; --t) {
+            uint32_t tl[16];
+            ld16(tbase + (uint32_t)((t - 2) * OBN + 16 * h), tl);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) y[j] = fma((double)__uint_as_float(rr[j]), w, y[j]);
-      }
-      if (r < M) {
-        const int er = rowexp[r];
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-          const int c = n0 + hc * 32 + j;
-          if (c >= N) break;
-          const int e = er + colexp[col0 + c];
-          // value = 2^{e} 2^{-35} (G1 + sum_{t>=6} 2^{-7(t-5)} L_t)
-          const double v0 = (nkb == 0) ? 0.0 : ldexp((double)g1[j] + y[j], e - OZ_B * 5);
-          if (partial) {
-            partial[(size_t)blockIdx.z * M * N + (size_t)r + (size_t)c * M] = v0;
-            continue;
+            for (int j = 0; j < 16; ++j) y[j] += (double)__uint_as_float(tl[j]);
           }
-          const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
-          double v = alpha * v0;
-          if (beta != 0.0) v = fma(beta, X64[idx], v);
-          if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
-          out64[idx] = v;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = 16 * h + jj;
+          const int c = n0 + cg * 32 + j;
+          if (r < M && c < N) {
+            const int e = er + colexp[col0 + c];
+            // value = 2^{e - 40} (G1 + 2^-8 sum_{t>=6} acc_t)
+            const double v0 =
+                (nkb == 0) ? 0.0 : ldexp(fma(y[jj], 1.0 / 256.0, (double)g1[j]), e - OZ_B * 5);
+            if (partial) {
+              partial[(size_t)blockIdx.z * M * N + (size_t)r + (size_t)c * M] = v0;
+            } else {
+              const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
+              double v = alpha * v0;
+              if (beta != 0.0) v = fma(beta, X64[idx], v);
+              if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
+              out64[idx] = v;
+            }
+          }
         }
       }
     }
@@ -300,10 +358,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
+    // every MMA has finished before the columns are released (the epilogue waited on the
+    // normal path; after an error this bounded wait covers MMAs still in flight)
+    if (nkb > 0 && !bar_wait(tdone, 0u) && lane == 0) atomicOr(s_err, 8);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
-  if (threadIdx.x == 0 && *s_err) atomicOr(&status->timeout, *s_err);
+  if (threadIdx.x == 32 && *s_err) atomicOr(&status->timeout, *s_err);
 }
 
 // Sum of the split-K partial results in a fixed order, then the three-term epilogue.
@@ -326,39 +387,71 @@ __global__ void oz_reduce_kernel(int M, int N, int S, const double* __restrict__
 
 // ---------------- slicing ----------------
 
-__device__ __forceinline__ int exp_bound(double amax) {
+// |x| as its IEEE bit pattern: for non-negative doubles the integer order is the numeric
+// order, so row / column maxima need no FP64 instructions (FP64 issues at 2 per clock per
+// SM here, integer work at 64).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+__device__ __forceinline__ int exp_bound(unsigned long long amax_bits) {
   // smallest e with amax < 2^e (0 for an all-zero row/column)
-  if (!(amax > 0.0)) return 0;
+  if (amax_bits == 0) return 0;
   int e;
-  frexp(amax, &e);  // amax = f 2^e, f in [0.5, 1)
+  frexp(__longlong_as_double((long long)amax_bits), &e);  // amax = f 2^e, f in [0.5, 1)
   return e;
 }
 
-// Digits by rounding to nearest: d_1 in [-128, 128], d_i in [-64, 64] for i > 1 (the
-// remainder after a nearest rounding is at most half a unit), all exact in BF16.  The
-// slicing error is then at most 2^-57 of the row / column scale and unbiased, so it
-// accumulates like a random walk over K instead of growing linearly as truncation's
-// one-signed error does.
+// Digits by rounding to nearest: d_1 in [-256, 256], d_i in [-128, 128] for i > 1 (the
+// remainder after a nearest rounding is at most half a unit), stored as d_i 2^{-8(i-3)},
+// all exact in BF16.  The slicing error is at most 2^-57 of the row / column scale and
+// unbiased, so it accumulates like a random walk over K instead of growing linearly as
+// truncation's one-signed error does.
+// Integer form: R = round(x 2^{56 - e}) (|R| < 2^56, from the significand and exponent
+// fields), then balanced base-256 digits from the top, d = floor((R + 2^{s-1}) / 2^s),
+// R -= d 2^s for s = 48, 40, ..., 8, and the last digit the remainder.
 __device__ __forceinline__ void write_digits(double x, int e, __nv_bfloat16* base, size_t idx,
                                              size_t plane) {
-  double r = ldexp(x, -e);  // |r| < 1, exact
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long m = bits & ((1LL << 52) - 1);
+  long long R = 0;
+  if (ex != 0x7FF) {
+    int sh;
+    if (ex == 0) {
+      sh = 1 - 1075 + 56 - e;  // subnormal: x = m 2^-1074
+    } else {
+      m |= 1LL << 52;
+      sh = ex - 1075 + 56 - e;  // x = m 2^{ex - 1075}; |x| < 2^e gives m 2^sh < 2^56
+    }
+    if (sh >= 0) R = m << sh;
+    else if (sh > -64) R = (m + (1LL << (-sh - 1))) >> (-sh);
+    if (bits < 0) R = -R;
+  }
 #pragma unroll
   for (int i = 0; i < OZ_S; ++i) {
-    const double s = r * 128.0;
-    const double d = rint(s);
-    r = s - d;
-    base[idx + (size_t)i * plane] = __double2bfloat16(d);
+    const int s = OZ_B * (OZ_S - 1 - i);
+    long long d = R;
+    if (s > 0) {
+      d = (R + (1LL << (s - 1))) >> s;
+      R -= d << s;
+    }
+    const float v = __int2float_rn((int)d) * __int_as_float((127 + OZ_B * (2 - i)) << 23);
+    base[idx + (size_t)i * plane] = __float2bfloat16_rz(v);  // exact: 8 significant bits
   }
 }
 
-__device__ __forceinline__ double block_max(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
-  if (lane == 0) red[w] = v;
+  if (lane == 0) red[wi] = v;
   __syncthreads();
-  double m = 0.0;
-  for (int i = 0; i < nw; ++i) m = fmax(m, red[i]);
+  unsigned long long m = 0;
+  for (int i = 0; i < nw; ++i) m = red[i] > m ? red[i] : m;
   return m;
 }
 
@@ -368,7 +461,7 @@ template <class T>
 __global__ void __launch_bounds__(256) oz_slice_A_kernel(int n, const T* __restrict__ A, int lda,
                                                          int kp, __nv_bfloat16* planes,
                                                          size_t plane, int* rowexp) {
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   const int M = Sc<T>::cplx ? 2 * n : n;
   const int m = blockIdx.x;
   const int mm = m % n;
@@ -382,10 +475,12 @@ __global__ void __launch_bounds__(256) oz_slice_A_kernel(int n, const T* __restr
       return A[(size_t)k + (size_t)m * lda];
     }
   };
-  double amax = 0.0;
-  for (int k = threadIdx.x; k < M; k += 256) amax = fmax(amax, fabs(elem(k)));
-  amax = block_max(amax, red);
-  const int e = exp_bound(amax);
+  unsigned long long amax = 0;
+  for (int k = threadIdx.x; k < M; k += 256) {
+    const unsigned long long b = abs_bits(elem(k));
+    amax = b > amax ? b : amax;
+  }
+  const int e = exp_bound(block_max(amax, red));
   if (threadIdx.x == 0) rowexp[m] = e;
   for (int k = threadIdx.x; k < kp; k += 256) {
     const double x = (k < M) ? elem(k) : 0.0;
@@ -398,13 +493,15 @@ __global__ void __launch_bounds__(256) oz_slice_A_kernel(int n, const T* __restr
 __global__ void __launch_bounds__(256) oz_slice_V_kernel(int M, int c0, const double* __restrict__ V64,
                                                          int ldi, int kp, __nv_bfloat16* planes,
                                                          size_t plane, int* colexp) {
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   const int c = c0 + blockIdx.x;
   const double* col = V64 + (size_t)c * ldi;
-  double amax = 0.0;
-  for (int k = threadIdx.x; k < M; k += 256) amax = fmax(amax, fabs(col[k]));
-  amax = block_max(amax, red);
-  const int e = exp_bound(amax);
+  unsigned long long amax = 0;
+  for (int k = threadIdx.x; k < M; k += 256) {
+    const unsigned long long b = abs_bits(col[k]);
+    amax = b > amax ? b : amax;
+  }
+  const int e = exp_bound(block_max(amax, red));
   if (threadIdx.x == 0) colexp[c] = e;
   for (int k = threadIdx.x; k < kp; k += 256) {
     const double x = (k < M) ? col[k] : 0.0;
@@ -439,7 +536,7 @@ template <class T>
 __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, int l, const T* __restrict__ Xt,
                                                             int ldt, int kp, __nv_bfloat16* planes,
                                                             size_t plane, int* rowexp) {
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   const int m = blockIdx.x;
   const int mm = Sc<T>::cplx ? (m % n) : m;
   const bool mre = !Sc<T>::cplx || m < n;
@@ -455,10 +552,12 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, int l, const 
       return row[k];
     }
   };
-  double amax = 0.0;
-  for (int k = threadIdx.x; k < K; k += 256) amax = fmax(amax, fabs(elem(k)));
-  amax = block_max(amax, red);
-  const int e = exp_bound(amax);
+  unsigned long long amax = 0;
+  for (int k = threadIdx.x; k < K; k += 256) {
+    const unsigned long long b = abs_bits(elem(k));
+    amax = b > amax ? b : amax;
+  }
+  const int e = exp_bound(block_max(amax, red));
   if (threadIdx.x == 0) rowexp[m] = e;
   for (int k = threadIdx.x; k < kp; k += 256) {
     const double x = (k < K) ? elem(k) : 0.0;
@@ -476,17 +575,22 @@ __global__ void __launch_bounds__(512) oz_slice_cols_kernel(int n, int q, const 
                                                             int ldy, int kp, bool pair,
                                                             __nv_bfloat16* planes, size_t plane,
                                                             int* colexp) {
-  __shared__ double red[16];
+  __shared__ unsigned long long red[16];
   const int j = blockIdx.x;
   const int M = Sc<T>::cplx ? 2 * n : n;
   const T* col = Y + (size_t)j * ldy;
-  double amax = 0.0;
+  unsigned long long amax = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    if constexpr (Sc<T>::cplx) amax = fmax(amax, fmax(fabs(col[i].x), fabs(col[i].y)));
-    else amax = fmax(amax, fabs(col[i]));
+    unsigned long long b;
+    if constexpr (Sc<T>::cplx) {
+      const unsigned long long b0 = abs_bits(col[i].x), b1 = abs_bits(col[i].y);
+      b = b0 > b1 ? b0 : b1;
+    } else {
+      b = abs_bits(col[i]);
+    }
+    amax = b > amax ? b : amax;
   }
-  amax = block_max(amax, red);
-  const int e = exp_bound(amax);
+  const int e = exp_bound(block_max(amax, red));
   if (threadIdx.x == 0) {
     colexp[j] = e;
     if (pair) colexp[q + j] = e;
@@ -550,7 +654,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-// 3-D BF16 map over S digit planes: {kp (contiguous), rows, S}, box {64, box_rows, 1};
+// 3-D BF16 map over S digit planes: {kp (contiguous), rows, S}, box {32, box_rows, 1};
 // consecutive planes are plane_rows * kp elements apart (plane_rows >= rows).
 int make_map3(CUtensorMap* map, const void* base, int kp, int rows, int plane_rows, int box_rows) {
   auto enc = encoder();
@@ -560,7 +664,7 @@ int make_map3(CUtensorMap* map, const void* base, int kp, int rows, int plane_ro
   cuuint32_t box[3] = {OBK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : CHASE_ERR_CUDA;
 }

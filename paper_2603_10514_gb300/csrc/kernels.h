@@ -91,8 +91,9 @@ int tc_filter_step(cudaStream_t st, int M, int kp, const void* Ah, const void* A
                    int* launches);
 
 // ---- FP64-accurate Ozaki-scheme products on BF16 tensor cores (gemm_oz.cu) -
-// 8 BF16 digit planes per operand.  A planes: row-major (M x kp), V planes:
+// 7 BF16 digit planes per operand.  A planes: row-major (M x kp), V planes:
 // column-major (kp x ncols_total).
+constexpr size_t kOzPlaneBytes = 14;  // bytes of digit planes per operand element
 template <class T>
 int oz_slice_A(cudaStream_t st, int n, const T* A, int lda, int kp, void* planes, int* rowexp,
                int* launches);

@@ -31,6 +31,38 @@ int fail_cuda(cudaError_t e, const char* what, const char* file, int line) {
 
 using namespace chase;
 
+// CUDA-event time of selected launches on one stream (the filter's product kernels):
+// event pairs around each launch, summed once the stream has been synchronised.
+struct LaunchTimer {
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  void begin(cudaStream_t st) {
+    while (ev.size() < used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      ev.push_back(e);
+    }
+    cudaEventRecord(ev[used], st);
+  }
+  void end(cudaStream_t st) {
+    if (ev.size() < used + 2) return;
+    cudaEventRecord(ev[used + 1], st);
+    used += 2;
+  }
+  double collect() {  // seconds; call after the stream has been synchronised
+    double s = 0.0;
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) s += ms;
+    }
+    used = 0;
+    return s * 1e-3;
+  }
+  ~LaunchTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
 struct chase_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -43,6 +75,7 @@ struct chase_ctx {
   size_t hbuf_bytes = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int launches = 0;
+  LaunchTimer product_timer;  // filter product launches of the current solve / call
 };
 
 namespace {
@@ -156,9 +189,11 @@ int filter_inplace(chase_ctx* h, int n, const T* A, int lda, int ncols, T* V, in
       gamma = -sigma * sn;
       sigma = sn;
     }
+    h->product_timer.begin(st);
     TRY(gemm<T>(st, false, n, act, n, A, lda, in + (size_t)first * ldi, ldi,
                 out + (size_t)first * ldo, ldo, alpha, beta, in + (size_t)first * ldi, ldi, gamma,
                 out + (size_t)first * ldo, ldo, scr, false, false, &h->launches));
+    h->product_timer.end(st);
     if (flops) *flops += per_col * act;
     if (steps) ++*steps;
   }
@@ -247,9 +282,11 @@ int filter_mixed(chase_ctx* h, int n, const T* A, int lda, bool split_A, int nco
       gamma = -sigma * sn;
       sigma = sn;
     }
+    h->product_timer.begin(st);
     TRY(tc_filter_step(st, M, kp, B.Ah, B.Al, B.Vh[in], B.Vl[in], ncols, first, act, alpha, beta,
                        B.V64[in], gamma, B.V64[out], B.V64[out], kp, B.Vh[out], B.Vl[out],
                        h->dstat, &h->launches));
+    h->product_timer.end(st);
     if (flops) *flops += per_col * act;
     if (steps) ++*steps;
   }
@@ -284,7 +321,7 @@ template <class T>
 size_t oz_bytes(int n, int ncols) {
   const int M = Sc<T>::cplx ? 2 * n : n;
   const size_t kp = (size_t)tc_kpad(M);
-  return align256(16 * (size_t)M * kp) + align256(4 * (size_t)M) + align256(16 * kp * ncols) +
+  return align256(kOzPlaneBytes * (size_t)M * kp) + align256(4 * (size_t)M) + align256(kOzPlaneBytes * kp * ncols) +
          align256(4 * (size_t)ncols) + 2 * align256(8 * kp * ncols);
 }
 
@@ -295,9 +332,9 @@ OzBufs oz_carve(char* base, int n, int ncols) {
   B.kp = tc_kpad(B.M);
   B.ncols = ncols;
   size_t off = 0;
-  B.Ap = base + off; off += align256(16 * (size_t)B.M * B.kp);
+  B.Ap = base + off; off += align256(kOzPlaneBytes * (size_t)B.M * B.kp);
   B.rowexp = (int*)(base + off); off += align256(4 * (size_t)B.M);
-  B.Vp = base + off; off += align256(16 * (size_t)B.kp * ncols);
+  B.Vp = base + off; off += align256(kOzPlaneBytes * (size_t)B.kp * ncols);
   B.colexp = (int*)(base + off); off += align256(4 * (size_t)ncols);
   for (int i = 0; i < 2; ++i) { B.V64[i] = (double*)(base + off); off += align256(8 * (size_t)B.kp * ncols); }
   return B;
@@ -335,8 +372,10 @@ int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols,
       sigma = sn;
     }
     TRY(oz_slice_V(st, M, first, ncols, B.V64[in], kp, kp, ncols, B.Vp, B.colexp, &h->launches));
+    h->product_timer.begin(st);
     TRY(oz_gemm(st, M, kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, ncols, first, act, alpha, beta,
                 B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, scr, &h->launches));
+    h->product_timer.end(st);
     if (flops) *flops += per_col * act;
     if (steps) ++*steps;
   }
@@ -390,8 +429,8 @@ size_t ozp_bytes(int n, int l) {
   const size_t kp = (size_t)tc_kpad(M);
   const size_t kpl = (size_t)tc_kpad(Sc<T>::cplx ? 2 * l : l);
   const size_t wl = Sc<T>::cplx ? 2 * (size_t)l : (size_t)l;
-  return align256(16 * kp * wl) + align256(4 * wl) + align256(16 * kp * l) + align256(4 * (size_t)l) +
-         align256(16 * (size_t)M * kpl) + align256(4 * (size_t)M) + align256(16 * kpl * l) +
+  return align256(kOzPlaneBytes * kp * wl) + align256(4 * wl) + align256(kOzPlaneBytes * kp * l) + align256(4 * (size_t)l) +
+         align256(kOzPlaneBytes * (size_t)M * kpl) + align256(4 * (size_t)M) + align256(kOzPlaneBytes * kpl * l) +
          align256(4 * (size_t)l) + align256(8 * kpl * l) +
          align256(8 * std::max<size_t>(M, wl) * l) + align256(sizeof(T) * (size_t)n * l);
 }
@@ -406,13 +445,13 @@ OzProd ozp_carve(char* base, int n, int l) {
   const size_t wl = Sc<T>::cplx ? 2 * (size_t)l : (size_t)l;
   size_t off = 0;
   auto take = [&](size_t b) { char* p = base + off; off += align256(b); return p; };
-  P.Gp = take(16 * (size_t)P.kp * wl);
+  P.Gp = take(kOzPlaneBytes * (size_t)P.kp * wl);
   P.gexp = (int*)take(4 * wl);
-  P.Lp = take(16 * (size_t)P.kp * l);
+  P.Lp = take(kOzPlaneBytes * (size_t)P.kp * l);
   P.lexp = (int*)take(4 * (size_t)l);
-  P.Rp = take(16 * (size_t)P.M * P.kpl);
+  P.Rp = take(kOzPlaneBytes * (size_t)P.M * P.kpl);
   P.rexp = (int*)take(4 * (size_t)P.M);
-  P.Bp = take(16 * (size_t)P.kpl * l);
+  P.Bp = take(kOzPlaneBytes * (size_t)P.kpl * l);
   P.bexp = (int*)take(4 * (size_t)l);
   P.B64 = (double*)take(8 * (size_t)P.kpl * l);
   P.out = (double*)take(8 * std::max<size_t>(P.M, wl) * l);
@@ -607,6 +646,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
   double* hr = h->hbuf + l;    // l residuals
 
   chase_stats S{};
+  h->product_timer.collect();  // drop events of an earlier call
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -674,6 +714,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
                              mu1, scr, &S.filter_flops, &S.filter_launches);
       phase_end(S.t_filter);
     }
+    S.t_filter_product += h->product_timer.collect();  // the phase end synchronised the stream
     if (rc) break;
     for (int a = k; a < l; ++a) matvecs += deg[a];
     if (cfg.filtered_hook) {

@@ -69,6 +69,31 @@ def test_one_step_is_fp64_accurate(cl, handle, complex_, n, ncols):
 
 
 @pytest.mark.parametrize("complex_", [False, True])
+def test_one_step_long_k_sampled(cl, handle, complex_):
+    """K = 8192 with enough output tiles (64 x 10) that no split of K is taken: every CTA
+    runs 64 exact chunks and the tail over the whole K.  Sampled rows against FP64 numpy
+    within the Ozaki bound, dense columns to 1e-13 normwise (an FP64 product's class)."""
+    n = 4096 if complex_ else 8192
+    ncols = 640
+    lam = W.spectrum_uniform(n, -3.0, 40.0, 13)
+    At = W.known_spectrum_matrix(lam, 13, complex_, device="cuda")
+    A = At.cpu().numpy()
+    V = W.start_block(n, ncols, 14, complex_)
+    c, e, l1 = 20.0, 21.0, -5.0
+    got = cl.chase_filter(handle, At, dev(V), [1] * ncols, c, e, l1,
+                          prec=cl.CHASE_FP64_EMU).cpu().numpy()
+    rows = np.sort(np.random.default_rng(5).choice(n, 256, replace=False))
+    s = 1.0 / (l1 - c)
+    ref = s * (A[rows] @ V - c * V[rows])
+    K = 2 * n if complex_ else n
+    bound = abs(s) * (K * 2.0 ** -53 * np.abs(A[rows]).max(axis=1)[:, None] * np.abs(V).max(axis=0)[None, :]
+                      + abs(c) * np.abs(V[rows]) * 2.0 ** -52)
+    assert (np.abs(got[rows] - ref) / bound).max() <= 1.0
+    err = np.linalg.norm(got[rows] - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert err.max() <= 1e-13, err.max()
+
+
+@pytest.mark.parametrize("complex_", [False, True])
 def test_filter_matches_oracle_fp64_tolerance(cl, handle, complex_):
     n = 517
     degs = [0, 1, 2, 2, 5, 8, 8, 13, 20, 20, 27, 36] + [36] * 60
