@@ -40,6 +40,11 @@ BF16_SUSTAINED_TFLOPS = 1717.0
 # BF16 digit products per real FP64 product in the Ozaki-scheme kernel: 7 digits per operand,
 # pairs (i, j) with i + j <= 8.
 OZAKI_PAIRS = 28
+# DRAM bytes (read + write) of one oz_gemm_kernel launch of the default workload (complex
+# n = 10000, 600 active columns), from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, 1 pass); profiles/oz_gemm_kernel_fp64_emu_n10000.md.  Launches with
+# fewer active columns read the same digit planes of A, which are 94 % of it.
+OZ_TRAFFIC_PER_LAUNCH = 7.86e9 + 0.097e9
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
@@ -556,7 +561,8 @@ def main():
                 "bound": "tensor", "achieved": achieved, "peak": BF16_SUSTAINED_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / BF16_SUSTAINED_TFLOPS if achieved else None,
                 "peak_source": "measured: cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
-                "traffic": None}
+                "traffic": (OZ_TRAFFIC_PER_LAUNCH if (lp == 0 and args.n == 10000 and
+                                                      args.prec == "fp64_emu") else None)}
     fp64_equiv = st["filter_flops"] / st["t_filter"] / 1e12 if st["t_filter"] > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

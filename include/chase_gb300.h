@@ -134,8 +134,10 @@ typedef struct {
 } chase_iter_log;
 
 /* Creates a handle bound to CUDA device `device`.  `cuda_stream` is a
- * cudaStream_t to order work on, or NULL for a new non-blocking stream owned
- * by the handle.  Returns CHASE_ERR_CUDA if the device cannot be used. */
+ * cudaStream_t to order work on (cudaStreamLegacy or cudaStreamPerThread for
+ * the default streams), or NULL for a new stream owned by the handle; that
+ * stream is a blocking one, so it is ordered with work on the legacy default
+ * stream.  Returns CHASE_ERR_CUDA if the device cannot be used. */
 int chase_create(chase_handle* h, int device, void* cuda_stream);
 
 /* Frees the handle's workspace and stream (if it owns one). */

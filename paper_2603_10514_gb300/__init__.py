@@ -26,6 +26,7 @@ CHASE_ERR_CUDA, CHASE_ERR_OOM, CHASE_ERR_TIMEOUT, CHASE_ERR_NONFINITE, CHASE_ERR
 CHASE_ERR_TOO_LARGE = 8
 CHASE_FILTER_NOALLOC_MAX_BYTES = 32 << 20
 QR_VARIANTS = {1: "cholqr1", 2: "cholqr2", 3: "shifted_cholqr2", 4: "householder"}
+CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 
 EXPORTED = ["chase_create", "chase_destroy", "chase_config_default", "chase_workspace_bytes",
             "chase_solve", "chase_filter", "chase_qr", "chase_qr_prec", "chase_cond_est",
@@ -161,7 +162,12 @@ class Handle:
     """Owns a chase_handle: a device, a CUDA stream and the device workspace."""
 
     def __init__(self, device=0, stream=None):
+        """stream: a cudaStream_t as an int (e.g. torch.cuda.current_stream().cuda_stream) or
+        None for a stream of the handle's own.  0, CUDA's legacy default stream (torch's default
+        stream), is passed as cudaStreamLegacy: the C ABI reads NULL as "make a new stream"."""
         self._h = ctypes.c_void_p()
+        if stream is not None and int(stream) == 0:
+            stream = CUDA_STREAM_LEGACY
         s = ctypes.c_void_p(stream) if stream is not None else None
         rc = lib().chase_create(ctypes.byref(self._h), int(device), s)
         if rc:

@@ -1024,7 +1024,9 @@ int chase_create(chase_handle* hp, int device, void* cuda_stream) {
   if (cuda_stream) {
     h->stream = (cudaStream_t)cuda_stream;
   } else {
-    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) { delete h; return CHASE_ERR_CUDA; }
+    // a blocking stream: ordered with work on the legacy default stream, so data the
+    // caller prepared there is complete before the handle's work reads it
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamDefault) != cudaSuccess) { delete h; return CHASE_ERR_CUDA; }
     h->own_stream = true;
   }
   if (cudaMalloc((void**)&h->dstat, sizeof(DevStatus)) != cudaSuccess ||
