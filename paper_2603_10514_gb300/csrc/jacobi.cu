@@ -8,8 +8,13 @@
 //   1. rot kernel: for pair (p, q) with g = H_pq = |g| e^{i phi},
 //        tau = (H_qq - H_pp) / (2|g|), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
 //        c = 1/sqrt(1 + t^2), s = t c,  J = [[c, s e^{i phi}], [-s e^{-i phi}, c]];
-//   2. apply kernel: H <- J^H H J, one thread per 2x2 block (pair_a, pair_b),
-//      and W <- W J, one thread per (row, pair).
+//   2. apply kernel: H <- J^H H J, one thread per 2x2 block (pair_a, pair_b) with
+//      a <= b, which also writes block (b, a) as the conjugate transpose (H stays
+//      exactly Hermitian, and half the FP64 arithmetic of a full update is spent:
+//      the rounds are FP64-bound on GB300, 2 FP64 FMAs per clock per SM), and
+//      W <- W J, one thread per (row, pair).
+// The rotation kernel runs one warp per CTA so that the FP64 square roots and
+// divisions of the l/2 rotations spread over many SMs.
 // Sweeps stop when the off-diagonal Frobenius norm is <= l 2^-53 ||H||_F (the
 // rounding level a parallel sweep leaves behind; eigenvalues are then accurate
 // to that level by Weyl's inequality) or after max_sweeps.
@@ -84,6 +89,7 @@ __global__ void jacobi_apply_kernel(int l, int L, const Rot* __restrict__ rots, 
        t += (long long)gridDim.x * blockDim.x) {
     if (t < nblk) {
       const int a = (int)(t % np), b = (int)(t / np);
+      if (a > b) continue;  // written by block (b, a) as its conjugate transpose
       const Rot ra = rots[a], rb = rots[b];
       const int pa = ra.p, qa = ra.q, pb = rb.p, qb = rb.q;
       const bool va = qa < l, vb = qb < l;
@@ -116,6 +122,12 @@ __global__ void jacobi_apply_kernel(int l, int L, const Rot* __restrict__ rots, 
       if (va) H[(size_t)qa + (size_t)pb * ldh] = o_qp;
       if (vb) H[(size_t)pa + (size_t)qb * ldh] = o_pq;
       if (va && vb) H[(size_t)qa + (size_t)qb * ldh] = o_qq;
+      if (a != b) {  // mirror: rows of pair b, columns of pair a
+        H[(size_t)pb + (size_t)pa * ldh] = Sc<T>::conj(o_pp);
+        if (va) H[(size_t)pb + (size_t)qa * ldh] = Sc<T>::conj(o_qp);
+        if (vb) H[(size_t)qb + (size_t)pa * ldh] = Sc<T>::conj(o_pq);
+        if (va && vb) H[(size_t)qb + (size_t)qa * ldh] = Sc<T>::conj(o_qq);
+      }
     } else {
       const long long u = t - nblk;
       const int i = (int)(u % l), b = (int)(u / l);
@@ -228,7 +240,7 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
   if (l > 1) {
     const long long work_items = (long long)(L / 2) * (L / 2) + (long long)l * (L / 2);
     const int ablocks = std::min(ceil_div(work_items, 256), kNumSMs * 8);
-    const int rblocks = ceil_div(L / 2, 128);
+    const int rblocks = ceil_div(L / 2, 32);
     for (sw = 0; sw < max_sweeps; ++sw) {
       jacobi_offnorm_kernel<T><<<1, 1024, 0, st>>>(l, H, ldh, dnrm);
       ++nl;
@@ -238,7 +250,7 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
       const double tolr = 1.1102230246251565e-16 * (double)l;
       if (host_nrm[0] <= tolr * tolr * host_nrm[1] || host_nrm[0] == 0.0) break;
       for (int r = 0; r < L - 1; ++r) {
-        jacobi_rot_kernel<T><<<rblocks, 128, 0, st>>>(l, L, r, H, ldh, rots);
+        jacobi_rot_kernel<T><<<rblocks, 32, 0, st>>>(l, L, r, H, ldh, rots);
         jacobi_apply_kernel<T><<<ablocks, 256, 0, st>>>(l, L, rots, H, ldh, W, ldw);
         nl += 2;
       }
