@@ -280,8 +280,10 @@ const char* chase_status_string(int status);
  *
  * Arguments as chase_filter (FP64 only), without a handle: the work is ordered
  * on `cuda_stream` (a cudaStream_t, NULL = legacy default stream) of the
- * current device, and the call returns after it completes.  The caller passes
- * and owns dV and dVout as before.
+ * current device, and the call returns after it completes; while `cuda_stream`
+ * is being captured into a CUDA graph the work is recorded and the call returns
+ * at once (replaying the graph runs the filter on the captured pointers).  The
+ * caller passes and owns dV and dVout as before.
  * Limits and behaviour:
  *   - sizeof(element) * n * ncols must be <= CHASE_FILTER_NOALLOC_MAX_BYTES,
  *     otherwise CHASE_ERR_TOO_LARGE is returned and nothing is done.

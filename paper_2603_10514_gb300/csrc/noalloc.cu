@@ -117,7 +117,11 @@ int run(cudaStream_t st, void* base, int n, const T* A, int lda, int ncols, cons
   }
   int rc = filter_fixed_scratch<T>(st, n, A, lda, ncols, out, ldo, P, deg, c, e, lambda1, scr);
   if (rc) return rc;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return CHASE_ERR_CUDA;
+  // while the stream is captured into a graph the work is only recorded: return at once
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return CHASE_ERR_CUDA;
+  if (cs == cudaStreamCaptureStatusNone && cudaStreamSynchronize(st) != cudaSuccess)
+    return CHASE_ERR_CUDA;
   return CHASE_OK;
 }
 

@@ -91,3 +91,34 @@ def test_noalloc_rejects_blocks_beyond_the_fixed_scratch(cl):
         cl.chase_filter_noalloc(A, V, [2] * ncols, 0.5, 0.6, -1.2, out=out)
     assert ex.value.code == cl.CHASE_ERR_TOO_LARGE
     assert bool((out == 7.0).all())
+
+
+def test_noalloc_filter_captures_into_a_cuda_graph(cl):
+    """Recorded once into a CUDA graph (global capture mode: an allocation would fail the
+    capture), replayed on new contents of the same input buffer: every replay matches
+    chase_filter on that input."""
+    n = 517
+    degs = [1, 2, 5, 8, 13, 20, 20, 36]
+    lam = W.spectrum_uniform(n, -1.0, 1.0, 9)
+    A = W.known_spectrum_matrix(lam, 9, True, device="cuda")
+    l1, le, bs = lam[0], lam[len(degs) - 1], lam[-1] + 1e-3
+    c, e = 0.5 * (bs + le), 0.5 * (bs - le)
+    Vs = _dev(W.start_block(n, len(degs), 10, True))
+    Out = torch.empty_like(Vs.mT).mT
+    cl.chase_filter_noalloc(A, Vs, degs, c, e, l1, out=Out)  # caches the scratch address
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        cl.chase_filter_noalloc(A, Vs, degs, c, e, l1, out=Out)
+    h = cl.Handle(0)
+    try:
+        for seed in (11, 12):
+            Vs.copy_(_dev(W.start_block(n, len(degs), seed, True)))
+            g.replay()
+            torch.cuda.synchronize()
+            ref = cl.chase_filter(h, A, Vs, degs, c, e, l1).cpu().numpy()
+            got = Out.cpu().numpy()
+            err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+            assert err.max() <= 1e-11, err.max()
+    finally:
+        h.close()
