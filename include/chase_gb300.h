@@ -42,15 +42,18 @@ typedef struct chase_ctx* chase_handle;
 
 typedef enum { CHASE_R64 = 0, CHASE_C128 = 1 } chase_dtype;
 
-/* Arithmetic of the A*V products (filter and Rayleigh-Ritz).
+/* Arithmetic of the block products.
  *   CHASE_FP64      native FP64 (DFMA) everywhere.
- *   CHASE_FP64_EMU  A*V products by the Ozaki scheme on the BF16 tensor cores:
- *                   8 exact 7-bit slices per operand, exact integer accumulation,
- *                   accurate to ~2^-53 |A||V| per entry like an FP64 product.
+ *   CHASE_FP64_EMU  every block product (filter A*V, Rayleigh-Ritz A*Q, Q^H(AQ), QW,
+ *                   (AQ)W, and the QR's Gram X^H X and X R^{-1}) by the Ozaki scheme
+ *                   on the BF16 tensor cores: 7 signed 8-bit digits per operand entry,
+ *                   exact integer accumulation of the leading levels, accurate to
+ *                   ~2^-53 |A||V| per entry like an FP64 product.
  *   CHASE_BF16X3    mixed: BF16x3 filter products (three BF16 tensor-core
  *                   products of hi/lo splits, FP32 accumulation) while the
- *                   residuals are large, then CHASE_FP64_EMU.
- * QR, the Rayleigh-Ritz Gram and residuals stay native FP64 in every mode. */
+ *                   residuals are large, then as CHASE_FP64_EMU.
+ * The Cholesky factor, its inverse, Householder QR, the Jacobi eigensolver and the
+ * residual norms are FP64 in every mode. */
 typedef enum { CHASE_FP64 = 0, CHASE_TF32 = 1, CHASE_BF16X3 = 2, CHASE_FP64_EMU = 3 } chase_precision;
 
 typedef enum {
