@@ -40,11 +40,11 @@ BF16_SUSTAINED_TFLOPS = 1717.0
 # BF16 digit products per real FP64 product in the Ozaki-scheme kernel: 7 digits per operand,
 # pairs (i, j) with i + j <= 8.
 OZAKI_PAIRS = 28
-# DRAM bytes (read + write) of one oz_gemm_kernel launch of the default workload (complex
-# n = 10000, 600 active columns), from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, 1 pass); profiles/oz_gemm_kernel_fp64_emu_n10000.md.  Launches with
-# fewer active columns read the same digit planes of A, which are 94 % of it.
-OZ_TRAFFIC_PER_LAUNCH = 7.86e9 + 0.097e9
+# DRAM bytes (read + write) of one Ozaki product (tail + exact-level kernel) of the default
+# workload (complex n = 10000, 600 active columns), from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass); None until taken for the current
+# kernels.
+OZ_TRAFFIC_PER_LAUNCH = None
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
@@ -556,7 +556,8 @@ def main():
         lp = st["filter_flops_lowprec"]
         tc_flops = OZAKI_PAIRS * (st["filter_flops"] - lp) + 3.0 * lp
         achieved = tc_flops / nl / dur_launch / 1e12 if dur_launch > 0 else None
-        roof = {"kernel": "oz_gemm_kernel (Ozaki-scheme FP64 product on BF16 tcgen05)" +
+        roof = {"kernel": "oz_part_kernel tail + exact levels (Ozaki-scheme FP64 product on "
+                          "BF16 tcgen05)" +
                           (" + tc_filter_bf16x3_kernel" if lp > 0 else ""),
                 "bound": "tensor", "achieved": achieved, "peak": BF16_SUSTAINED_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / BF16_SUSTAINED_TFLOPS if achieved else None,

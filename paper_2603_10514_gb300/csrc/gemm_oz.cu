@@ -31,19 +31,23 @@
 // The result is A*V to within ~2^-53 K max|A_m.| max|V_.c| per entry, the
 // accuracy class of an FP64 GEMM.
 //
-// Kernel: one CTA per 128 x 64 output tile, 320 threads:
-//   warp 0     TMA producer: per 32-wide K block one stage holding the 7 A digit
-//              tiles (128 x 32 BF16) and the 7 V digit tiles (64 x 32), two
-//              stages (84 KB each, 64-byte swizzle);
-//   warp 1     allocates 512 TMEM columns (7 level accumulators x 64) and issues
-//              the tcgen05.mma.kind::f16 (M 128, N 64, K 16): 56 per K block.
-//              The exact levels are issued before the tail levels in the last
-//              block of a chunk and after them in the first, so the epilogue
-//              reads a finished chunk while the tensor core works on the tail;
-//   warps 2-9  epilogue: 4 lane quarters x 2 column halves; per chunk a
-//              tcgen05.ld of levels 2..5 and exact int64 accumulation; at the
-//              end levels 6..8, the FP64 recombination and the Chebyshev
-//              three-term update.
+// Two kernels per product (oz_part_kernel), 320 threads each: a TMA producer warp,
+// an MMA warp that allocates TMEM and issues tcgen05.mma.kind::f16 (M 128, K 16)
+// from one thread, and 8 epilogue warps reading TMEM with tcgen05.ld.
+//   * tail (levels 6..8): 128 x 128 tiles, 3 accumulators x 128 TMEM columns,
+//     two 112 KB stages of all 7 A and 7 V digit tiles per 32-wide K block, 36
+//     MMAs per block; K may be split freely; writes 2^{e-48} sum_t acc_t per
+//     output (one FP64 slab per split).
+//   * exact (levels 2..5): 128 x 64 tiles, digit planes 1..4 only (no pair of
+//     these levels uses a higher digit), four 48 KB stages, 20 MMAs per block;
+//     two sets of the 4 level accumulators (2 x 4 x 64 columns) so that the
+//     epilogue converts one 128-wide K chunk (32-bit conversions, shifted into an
+//     int64 per output) while the next accumulates; adds the tail values and
+//     applies the Chebyshev three-term update (or writes split-K partials).
+// Measured on GB300 (probes with the digit-pair patterns fed from shared memory):
+// 48 cycles per M128 N64 K16 MMA for 7 interleaved accumulators, 32 per N64
+// equivalent at N = 128 with 3 accumulators; the split runs the 18 tail pairs at
+// the wider tile.
 // Digit slicing is integer arithmetic on the FP64 bit patterns (FP64 issues at
 // 2 per clock per SM on this part; the integer pipes at 64).
 // All mbarrier waits are bounded; on expiry the kernel records the failure in
@@ -65,20 +69,11 @@ namespace {
 constexpr int OZ_S = 7;          // digits per entry
 constexpr int OZ_B = 8;          // bits per digit
 constexpr int OZ_T0 = 6;         // first tail level; digit i is stored as d_i 2^{-8(i - 3)}
-constexpr int OZ_NACC = OZ_S;    // one accumulator per level t = 2..8
-constexpr int OBM = 128, OBN = 64, OBK = 32;
+constexpr int OBM = 128, OBK = 32;
 constexpr int OZ_CHUNK_KB = 4;   // 4 K blocks = 128 K per exact chunk
-constexpr int A_TILE = OBM * OBK * 2;           // 8 KB
-constexpr int V_TILE = OBN * OBK * 2;           // 4 KB
-constexpr int STAGE = OZ_S * (A_TILE + V_TILE); // 84 KB
-constexpr int NSTAGE = 2;
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
-constexpr int OZ_SMEM = NSTAGE * STAGE + 1024 + 256;
 constexpr long long kOzWait = 4000000000LL;
-static_assert(OZ_NACC * OBN <= 512, "accumulators exceed TMEM");
-static_assert(STAGE % 1024 == 0 && A_TILE % 512 == 0 && V_TILE % 512 == 0, "tile alignment");
-static_assert(OZ_SMEM <= 232448, "shared memory");
 static_assert(kOzPlaneBytes == 2 * OZ_S, "workspace plane size");
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -125,14 +120,6 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t a) {
   return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OBN >> 3) << 17) |
-                            ((uint32_t)(OBM >> 4) << 24);
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
-}
 __device__ __forceinline__ void commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    s32(b))
@@ -162,58 +149,99 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// MMAs of one K block for the pairs of the exact levels (t = 2..5) or of the tail
-// (t = 6..8), in level order; each pair is 2 K-steps of 16.  restart: the first MMA into
-// each accumulator overwrites it (exact: at a chunk start; tail: at the first block).
+// ---------------------------------------------------------------------------
+// Level-split product: the exact levels 2..5 and the tail levels 6..8 as two
+// kernels.  The tail kernel needs no per-chunk readout, so with three
+// accumulators it runs 128-wide N tiles (3 x 128 TMEM columns), which the tensor
+// core feeds ~1.5x faster per flop than 64-wide ones; it may split K freely and
+// writes its FP64 values (one slab per split) for the exact kernel.  The exact
+// kernel reads only digit planes 1..4 of each operand (no pair of levels 2..5 uses
+// a higher digit), keeps two sets of its four level accumulators (2 x 4 x 64 TMEM
+// columns) so that the epilogue reads one chunk while the next accumulates, and
+// adds the tail values before the three-term update.
+// ---------------------------------------------------------------------------
 template <bool kTail>
-__device__ __forceinline__ void issue_pairs(uint32_t tmem, uint64_t da0, uint64_t dv0, bool restart) {
+struct PartCfg {
+  static constexpr int BN = kTail ? 128 : 64;
+  static constexpr int PLANES = kTail ? OZ_S : 4;          // digit planes read
+  static constexpr int NST = kTail ? 2 : 4;                // stages
+  static constexpr int A_T = OBM * OBK * 2;                // 8 KB
+  static constexpr int V_T = BN * OBK * 2;                 // 4 or 8 KB
+  static constexpr int STG = PLANES * (A_T + V_T);         // 48 or 112 KB
+  static constexpr int SMEM = NST * STG + 1024 + 256;
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(OBM >> 4) << 24);
+};
+static_assert(PartCfg<true>::SMEM <= 232448 && PartCfg<false>::SMEM <= 232448, "shared memory");
+static_assert(3 * PartCfg<true>::BN <= 512 && 2 * 4 * PartCfg<false>::BN <= 512, "TMEM");
+static_assert(PartCfg<true>::STG % 1024 == 0 && PartCfg<false>::STG % 1024 == 0, "stage alignment");
+
+__device__ __forceinline__ void mma_n(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                      uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// MMAs of one K block of the part's levels.  Accumulator of level t: tail t - 6 at
+// column (t - 6) BN; exact t - 2 at column buf 4 BN + (t - 2) BN.  restart: the first
+// MMA into each accumulator (pair i = 1, K-step 0) overwrites it.
+template <bool kTail>
+__device__ __forceinline__ void issue_part(uint32_t tmem, uint32_t buf, uint64_t da0, uint64_t dv0,
+                                           bool restart) {
+  using C = PartCfg<kTail>;
 #pragma unroll
   for (int t = kTail ? OZ_T0 : 2; t <= (kTail ? OZ_S + 1 : OZ_T0 - 1); ++t) {
 #pragma unroll
     for (int i = 1; i <= OZ_S; ++i) {
       const int j = t - i;
       if (j < 1 || j > OZ_S) continue;
-      const uint32_t acc_col = (uint32_t)((t - 2) * OBN);
-      const bool first = (i == 1);
-      const uint64_t da = da0 + (uint64_t)(((i - 1) * A_TILE) >> 4);
-      const uint64_t dv = dv0 + (uint64_t)(((j - 1) * V_TILE) >> 4);
+      const uint32_t col = kTail ? (uint32_t)((t - OZ_T0) * C::BN)
+                                 : (uint32_t)(buf * 4 * C::BN + (t - 2) * C::BN);
+      const uint64_t da = da0 + (uint64_t)(((i - 1) * C::A_T) >> 4);
+      const uint64_t dv = dv0 + (uint64_t)(((j - 1) * C::V_T) >> 4);
 #pragma unroll
       for (int kk = 0; kk < OBK / 16; ++kk) {
         const uint64_t off = (uint64_t)((kk * 32) >> 4);
-        mma(tmem + acc_col, da + off, dv + off, (first && kk == 0 && restart) ? 0u : 1u);
+        mma_n(tmem + col, da + off, dv + off, C::IDESC, (i == 1 && kk == 0 && restart) ? 0u : 1u);
       }
     }
   }
 }
 
+// kTail: tail[z][r + c M] = 2^{e - 48} sum_{t >= 6} acc_t over this CTA's K range (z = split).
+// !kTail: v = 2^{e - 40} G1 (+ sum_z tail[z] when this is split 0), then partial[z] or the
+// three-term update into out64.
+template <bool kTail>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
+    oz_part_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
                    int M, int N, int nkb_total, int kbs, int col0, const int* __restrict__ rowexp,
                    const int* __restrict__ colexp, double alpha, double beta, const double* X64,
                    double gamma, const double* Z64, double* out64, int ldo,
-                   double* __restrict__ partial, DevStatus* status) {
+                   double* __restrict__ partial, double* tail, int tail_splits,
+                   DevStatus* status) {
+  using C = PartCfg<kTail>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + NSTAGE * STAGE);
-  uint64_t* full = bars;                              // [2] stage loaded
-  uint64_t* empty = bars + 2;                         // [2] stage consumed by the MMAs
-  uint64_t* cfull = bars + 4;                         // exact levels of a chunk accumulated
-  uint64_t* cfree = bars + 5;                         // exact levels read out of TMEM
-  uint64_t* tdone = bars + 6;                         // every MMA of the CTA finished
-  uint32_t* tslot = (uint32_t*)(bars + 7);
+  uint64_t* bars = (uint64_t*)(smem + C::NST * C::STG);
+  uint64_t* full = bars;                 // [NST]
+  uint64_t* empty = bars + C::NST;       // [NST]
+  uint64_t* cfull = bars + 2 * C::NST;   // [2] exact chunk accumulated in buffer b
+  uint64_t* cfree = cfull + 2;           // [2] buffer b read out
+  uint64_t* tdone = cfree + 2;           // every MMA finished
+  uint32_t* tslot = (uint32_t*)(tdone + 1);
   int* s_err = (int*)(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * OBN, m0 = blockIdx.y * OBM;
-  // split-K: this CTA's K blocks are [kbeg, kbeg + nkb), a whole number of exact chunks
+  const int n0 = blockIdx.x * C::BN, m0 = blockIdx.y * OBM;
   const int kbeg = blockIdx.z * kbs;
   const int nkb = max(0, min(kbs, nkb_total - kbeg));
   const int nchunks = (nkb + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NSTAGE; ++i) { bar_init(&full[i], 1); bar_init(&empty[i], 1); }
-    bar_init(cfull, 1);
-    bar_init(cfree, OZ_EPI_WARPS);  // one arrival per epilogue warp
+    for (int i = 0; i < C::NST; ++i) { bar_init(&full[i], 1); bar_init(&empty[i], 1); }
+    for (int b = 0; b < 2; ++b) { bar_init(&cfull[b], 1); bar_init(&cfree[b], OZ_EPI_WARPS); }
     bar_init(tdone, 1);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -233,18 +261,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ---------------- producer ----------------
     int issued = 0;
     for (int kb = 0; kb < nkb && !*(volatile int*)s_err; ++kb) {
-      const int s = kb & 1;
-      if (!bar_wait(&empty[s], (uint32_t)(((kb >> 1) & 1) ^ 1))) { atomicOr(s_err, 1); break; }
-      bar_expect(&full[s], STAGE);
-      unsigned char* st = smem + s * STAGE;
+      const int s = kb % C::NST;
+      if (!bar_wait(&empty[s], (uint32_t)(((kb / C::NST) & 1) ^ 1))) { atomicOr(s_err, 1); break; }
+      bar_expect(&full[s], C::STG);
+      unsigned char* st = smem + s * C::STG;
       const int x = (kbeg + kb) * OBK;
-      for (int i = 0; i < OZ_S; ++i) tma3(st + i * A_TILE, &mapA, &full[s], x, m0, i);
-      for (int j = 0; j < OZ_S; ++j) tma3(st + OZ_S * A_TILE + j * V_TILE, &mapV, &full[s], x, col0 + n0, j);
+      for (int i = 0; i < C::PLANES; ++i) tma3(st + i * C::A_T, &mapA, &full[s], x, m0, i);
+      for (int j = 0; j < C::PLANES; ++j)
+        tma3(st + C::PLANES * C::A_T + j * C::V_T, &mapV, &full[s], x, col0 + n0, j);
       issued = kb + 1;
     }
-    // copies still in flight land before the CTA can exit (already done on the normal path)
-    for (int b = max(0, issued - NSTAGE); b < issued; ++b)
-      if (!bar_wait(&full[b & 1], (uint32_t)((b >> 1) & 1))) atomicOr(s_err, 1);
+    for (int b = max(0, issued - C::NST); b < issued; ++b)
+      if (!bar_wait(&full[b % C::NST], (uint32_t)((b / C::NST) & 1))) atomicOr(s_err, 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     bool bad = false;
@@ -252,95 +280,103 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int chunk = kb / OZ_CHUNK_KB;
       const bool chunk_start = (kb % OZ_CHUNK_KB) == 0;
       const bool chunk_last = (kb % OZ_CHUNK_KB) == OZ_CHUNK_KB - 1 || kb == nkb - 1;
-      const int s = kb & 1;
-      if (!bar_wait(&full[s], (uint32_t)((kb >> 1) & 1))) { bad = true; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = s32(smem + s * STAGE);
-      const uint64_t da0 = desc_sw64(sa), dv0 = desc_sw64(sa + OZ_S * A_TILE);
-      if (chunk_start) {
-        // tail first: the epilogue may still be reading the previous chunk's exact levels
-        issue_pairs<true>(tmem, da0, dv0, kb == 0);
-        if (chunk > 0) {
-          if (!bar_wait(cfree, (uint32_t)((chunk - 1) & 1))) { bad = true; break; }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        }
-        issue_pairs<false>(tmem, da0, dv0, true);
-        if (chunk_last) commit(cfull);
-      } else {
-        issue_pairs<false>(tmem, da0, dv0, false);
-        if (chunk_last) commit(cfull);
-        issue_pairs<true>(tmem, da0, dv0, false);
+      const uint32_t buf = (uint32_t)(chunk & 1);
+      if (!kTail && chunk_start && chunk >= 2) {
+        // the epilogue has read this buffer's previous chunk (chunk - 2)
+        if (!bar_wait(&cfree[buf], (uint32_t)(((chunk - 2) >> 1) & 1))) { bad = true; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
+      const int s = kb % C::NST;
+      if (!bar_wait(&full[s], (uint32_t)((kb / C::NST) & 1))) { bad = true; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = s32(smem + s * C::STG);
+      const uint64_t da0 = desc_sw64(sa), dv0 = desc_sw64(sa + C::PLANES * C::A_T);
+      issue_part<kTail>(tmem, buf, da0, dv0, kTail ? (kb == 0) : chunk_start);
+      if (!kTail && chunk_last) commit(&cfull[buf]);
       commit(&empty[s]);
     }
     if (bad) atomicOr(s_err, 2);
-    commit(tdone);  // arrives once every MMA issued above has completed
+    commit(tdone);
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int q = warp & 3;             // TMEM lane quarter this warp may access
-    const int cg = (warp - 2) >> 2;     // column group of 32
-    const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cg * 32);
-    long long g1[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) g1[j] = 0;
+    const int q = warp & 3;
+    const int cg = (warp - 2) >> 2;  // column half of the tile
+    const int r = m0 + 32 * q + lane;
+    const int er = (r < M) ? rowexp[r] : 0;
     bool ok = true;
-    // waits are taken by every lane and made warp-uniform: the tcgen05.ld below are
-    // .sync.aligned and must be executed by the whole warp or not at all
-    for (int c = 0; c < nchunks && ok; ++c) {
-      if (!__all_sync(0xffffffffu, bar_wait(cfull, (uint32_t)(c & 1)))) {
+    if constexpr (kTail) {
+      if (nkb > 0 && !__all_sync(0xffffffffu, bar_wait(tdone, 0u))) {
         ok = false;
         if (lane == 0) atomicOr(s_err, 4);
-        break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (__shfl_sync(0xffffffffu, (int)(ok && !*(volatile int*)s_err), 0)) {
+        double* tz = tail + (size_t)blockIdx.z * M * N;
 #pragma unroll 1
-      for (int t = 2; t < OZ_T0; ++t) {
-        uint32_t r[32];
-        ld32(tbase + (uint32_t)((t - 2) * OBN), r);
-        // accumulator = L_t 2^{8(6 - t)} with |L_t| < 2^24: a 32-bit conversion recovers L_t
-        // exactly; G1 counts in units of level 5, L_t 2^{8(5 - t)}
-        const float unscale = __int_as_float((127 - OZ_B * (OZ_T0 - t)) << 23);
+        for (int h = 0; h < C::BN / 2 / 16; ++h) {  // 4 groups of 16 columns of this half
+          const int cbase = cg * (C::BN / 2) + 16 * h;
+          double y[16];
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          g1[j] += (long long)__float2int_rz(__uint_as_float(r[j]) * unscale) << (OZ_B * (OZ_T0 - 1 - t));
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0 && c + 1 < nchunks) bar_arrive(cfree);
-    }
-    if (ok && nkb > 0 && !__all_sync(0xffffffffu, bar_wait(tdone, 0u))) {
-      ok = false;
-      if (lane == 0) atomicOr(s_err, 4);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int r = m0 + 32 * q + lane;
-    if (nkb == 0) ok = true;  // empty split: contributes zeros
-    if (__shfl_sync(0xffffffffu, (int)(ok && !*(volatile int*)s_err), 0)) {
-      const int er = (r < M) ? rowexp[r] : 0;
-      // two halves of 16 columns keep g1 and the tail levels in registers
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        double y[16];  // tail levels, summed smallest first, in units of level 5 times 2^8
-#pragma unroll
-        for (int j = 0; j < 16; ++j) y[j] = 0.0;
-        if (nkb > 0) {
+          for (int j = 0; j < 16; ++j) y[j] = 0.0;
+          if (nkb > 0) {
 #pragma unroll 1
-          for (int t = OZ_S + 1; t >= OZ_T0; --t) {
-            uint32_t tl[16];
-            ld16(tbase + (uint32_t)((t - 2) * OBN + 16 * h), tl);
+            for (int t = OZ_S + 1; t >= OZ_T0; --t) {
+              uint32_t tl[16];
+              ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((t - OZ_T0) * C::BN + cbase), tl);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) y[j] += (double)__uint_as_float(tl[j]);
+              for (int j = 0; j < 16; ++j) y[j] += (double)__uint_as_float(tl[j]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = n0 + cbase + j;
+            if (r < M && c < N) {
+              const int e = er + colexp[col0 + c];
+              tz[(size_t)r + (size_t)c * M] = ldexp(y[j], e - OZ_B * 6);  // 2^{e-40} 2^-8 sum
+            }
           }
         }
+      }
+    } else {
+      long long g1[32];
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int j = 16 * h + jj;
+      for (int j = 0; j < 32; ++j) g1[j] = 0;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const uint32_t buf = (uint32_t)(c & 1);
+        if (!__all_sync(0xffffffffu, bar_wait(&cfull[buf], (uint32_t)((c >> 1) & 1)))) {
+          ok = false;
+          if (lane == 0) atomicOr(s_err, 4);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + buf * 4 * C::BN + (uint32_t)(cg * 32);
+#pragma unroll 1
+        for (int t = 2; t < OZ_T0; ++t) {
+          uint32_t rr[32];
+          ld32(tb + (uint32_t)((t - 2) * C::BN), rr);
+          const float unscale = __int_as_float((127 - OZ_B * (OZ_T0 - t)) << 23);
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            g1[j] += (long long)__float2int_rz(__uint_as_float(rr[j]) * unscale) << (OZ_B * (OZ_T0 - 1 - t));
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0 && c + 2 < nchunks) bar_arrive(&cfree[buf]);
+      }
+      if (ok && nkb > 0 && !__all_sync(0xffffffffu, bar_wait(tdone, 0u))) {
+        ok = false;
+        if (lane == 0) atomicOr(s_err, 4);
+      }
+      if (nkb == 0) ok = true;
+      if (__shfl_sync(0xffffffffu, (int)(ok && !*(volatile int*)s_err), 0) && r < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
           const int c = n0 + cg * 32 + j;
-          if (r < M && c < N) {
+          if (c < N) {
             const int e = er + colexp[col0 + c];
-            // value = 2^{e - 40} (G1 + 2^-8 sum_{t>=6} acc_t)
-            const double v0 =
-                (nkb == 0) ? 0.0 : ldexp(fma(y[jj], 1.0 / 256.0, (double)g1[j]), e - OZ_B * 5);
+            double v0 = (nkb == 0) ? 0.0 : ldexp((double)g1[j], e - OZ_B * 5);
+            if (blockIdx.z == 0)
+              for (int z = 0; z < tail_splits; ++z) v0 += tail[(size_t)z * M * N + (size_t)r + (size_t)c * M];
             if (partial) {
               partial[(size_t)blockIdx.z * M * N + (size_t)r + (size_t)c * M] = v0;
             } else {
@@ -358,8 +394,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
-    // every MMA has finished before the columns are released (the epilogue waited on the
-    // normal path; after an error this bounded wait covers MMAs still in flight)
     if (nkb > 0 && !bar_wait(tdone, 0u) && lane == 0) atomicOr(s_err, 8);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -697,28 +731,48 @@ int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ld
 int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
             int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
-            DevStatus* dst, Scratch scr, int* launches) {
+            DevStatus* dst, Scratch scr, Scratch tailbuf, int* launches) {
   if (N <= 0) return 0;
-  CUtensorMap mA, mV;
+  CUtensorMap mA, mV64, mV128;
   if (a_plane_rows < M) a_plane_rows = M;
   if (make_map3(&mA, Aplanes, kp, M, a_plane_rows, OBM) ||
-      make_map3(&mV, Vplanes, kp, ncols_total, ncols_total, OBN))
+      make_map3(&mV64, Vplanes, kp, ncols_total, ncols_total, PartCfg<false>::BN) ||
+      make_map3(&mV128, Vplanes, kp, ncols_total, ncols_total, PartCfg<true>::BN))
     return CHASE_ERR_CUDA;
-  CHASE_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      OZ_SMEM));
+  CHASE_CUDA_TRY(cudaFuncSetAttribute(oz_part_kernel<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      PartCfg<true>::SMEM));
+  CHASE_CUDA_TRY(cudaFuncSetAttribute(oz_part_kernel<false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      PartCfg<false>::SMEM));
   const int nkb = kp / OBK;
-  const int tiles = ceil_div(N, OBN) * ceil_div(M, OBM);
-  // split K (in whole exact chunks) until there are about four waves of CTAs
+  const size_t slab = (size_t)M * N * sizeof(double);
+  if (slab > tailbuf.bytes) return CHASE_ERR_OOM;
+  // tail levels: split K freely (no exact chunks) up to about four waves of CTAs, one
+  // slab of FP64 values per split
+  const int tiles_t = ceil_div(N, PartCfg<true>::BN) * ceil_div(M, OBM);
+  int St = std::max(1, std::min(nkb, ceil_div(4 * kNumSMs, tiles_t)));
+  while (St > 1 && (size_t)St * slab > tailbuf.bytes) --St;
+  const int kbs_t = ceil_div(nkb, St);
+  St = ceil_div(nkb, kbs_t);
+  double* tail = (double*)tailbuf.ptr;
+  dim3 grid_t(ceil_div(N, PartCfg<true>::BN), ceil_div(M, OBM), St);
+  oz_part_kernel<true><<<grid_t, OZ_THREADS, PartCfg<true>::SMEM, st>>>(
+      mA, mV128, M, N, nkb, kbs_t, col0, rowexp, colexp, 0.0, 0.0, nullptr, 0.0, nullptr, nullptr, 0,
+      nullptr, tail, 0, dst);
+  if (launches) ++*launches;
+  // exact levels: split K in whole chunks until there are about four waves of CTAs
+  const int tiles = ceil_div(N, PartCfg<false>::BN) * ceil_div(M, OBM);
   const int nchunks = ceil_div(nkb, OZ_CHUNK_KB);
   int S = std::max(1, std::min(nchunks, ceil_div(4 * kNumSMs, tiles)));
-  while (S > 1 && (size_t)S * M * N * sizeof(double) > scr.bytes) --S;
+  while (S > 1 && (size_t)S * slab > scr.bytes) --S;
   const int kbs = ceil_div(nchunks, S) * OZ_CHUNK_KB;
   S = ceil_div(nkb, kbs);
   double* partial = (S > 1) ? (double*)scr.ptr : nullptr;
-  dim3 grid(ceil_div(N, OBN), ceil_div(M, OBM), S);
-  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, st>>>(mA, mV, M, N, nkb, kbs, col0, rowexp, colexp,
-                                                    alpha, beta, X64, gamma, Z64, out64, ldo,
-                                                    partial, dst);
+  dim3 grid(ceil_div(N, PartCfg<false>::BN), ceil_div(M, OBM), S);
+  oz_part_kernel<false><<<grid, OZ_THREADS, PartCfg<false>::SMEM, st>>>(
+      mA, mV64, M, N, nkb, kbs, col0, rowexp, colexp, alpha, beta, X64, gamma, Z64, out64, ldo,
+      partial, tail, St, dst);
   if (launches) ++*launches;
   if (S > 1) {
     const size_t total = (size_t)M * N;

@@ -117,11 +117,13 @@ int oz_gram_assemble(cudaStream_t st, int l, const double* out, int ldo, T* G, i
 template <class T>
 int transpose(cudaStream_t st, int n, int l, const T* X, int ldx, T* Xt, int ldt, int* launches);
 // out64[:, col0 + c] = alpha * (A V)[:, col0 + c] + beta * X64 + gamma * Z64 for c < N.
-// A's planes are a_plane_rows * kp elements apart (0: M * kp).
+// A's planes are a_plane_rows * kp elements apart (0: M * kp).  scr: split-K partials of
+// the exact levels; tailbuf: FP64 values of the tail levels, at least M * N doubles (more
+// lets the tail kernel split K).
 int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
             int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
-            DevStatus* dst, Scratch scr, int* launches);
+            DevStatus* dst, Scratch scr, Scratch tailbuf, int* launches);
 
 // ---- Lanczos spectral bounds (lanczos.cu) ----------------------------------
 // out = {lambda1, lambda_ell, b_sup} from nruns runs of m steps started at V0's columns.
