@@ -42,9 +42,10 @@ BF16_SUSTAINED_TFLOPS = 1717.0
 OZAKI_PAIRS = 28
 # DRAM bytes (read + write) of one Ozaki product (tail + exact-level kernel) of the default
 # workload (complex n = 10000, 600 active columns), from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass); None until taken for the current
-# kernels.
-OZ_TRAFFIC_PER_LAUNCH = None
+# (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass): tail 6.83 GB + 0.097 GB, exact
+# 4.63 GB + 0.094 GB; profiles/oz_part_kernel_fp64_emu_n10000.md.  Launches with fewer active
+# columns read the same digit planes of A, which are most of it.
+OZ_TRAFFIC_PER_LAUNCH = 6.83e9 + 0.097e9 + 4.63e9 + 0.094e9
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
