@@ -34,9 +34,19 @@ METRIC = ("time-to-solution for nev pairs at resid<=1e-10 & filter TFLOP/s vs FP
 # FP64 DFMA peak of GB300 derived from unit counts and the maximum SM clock:
 # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (a DFMA probe measured 1.203 TFLOP/s at ~2.0 GHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# Dense BF16 tensor peak measured on the GB300s (cuBLAS, burst), MEASURED_PEAKS.json.
-BF16_PEAK_TFLOPS = 1978.3
-BF16_SUSTAINED_TFLOPS = 1717.0
+# Dense BF16 tensor peaks measured on GB300 with cuBLAS (burst, and back to back for seconds
+# under the power cap), read from MEASURED_PEAKS.json next to this file when it is present;
+# the numbers below are the ones it held when this was written.
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"])
+    except (OSError, KeyError, ValueError, TypeError):
+        return 1978.3, 1717.0
+
+
+BF16_PEAK_TFLOPS, BF16_SUSTAINED_TFLOPS = _measured_peaks()
 # BF16 digit products per real FP64 product in the Ozaki-scheme kernel: 7 digits per operand,
 # pairs (i, j) with i + j <= 8.
 OZAKI_PAIRS = 28
