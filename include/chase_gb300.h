@@ -263,6 +263,19 @@ int chase_lanczos_bounds(chase_handle h, chase_dtype dtype, int n, const void* d
 /* Static description of a status code. */
 const char* chase_status_string(int status);
 
+/*
+ * chase_selftest_wait_timeout -- checks the failure path of the library's
+ * bounded device waits without causing a fault (the paper has no counterpart;
+ * it is a diagnostic of this implementation).  One device thread waits, for at
+ * most `seconds` (0 < seconds <= 10), on a barrier that nothing completes,
+ * gives up and records the timeout in the handle's device status word, the way
+ * the tensor-core kernels do when a copy or an MMA never completes.  Returns
+ * CHASE_ERR_TIMEOUT when the wait ran out and was reported (the expected
+ * result), CHASE_OK if it was not, CHASE_ERR_CUDA on a CUDA failure; the
+ * status word is cleared again and the handle stays usable.
+ */
+int chase_selftest_wait_timeout(chase_handle h, double seconds);
+
 /* Size of the fixed device scratch array behind chase_filter_noalloc (32 MiB). */
 #define CHASE_FILTER_NOALLOC_MAX_BYTES ((size_t)32 << 20)
 

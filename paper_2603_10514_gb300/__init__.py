@@ -31,7 +31,8 @@ CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 EXPORTED = ["chase_create", "chase_destroy", "chase_config_default", "chase_workspace_bytes",
             "chase_solve", "chase_filter", "chase_qr", "chase_qr_prec", "chase_cond_est",
             "chase_status_string",
-            "chase_filter_noalloc", "chase_reserve_workspace", "chase_lanczos_bounds"]
+            "chase_filter_noalloc", "chase_reserve_workspace", "chase_lanczos_bounds",
+            "chase_selftest_wait_timeout"]
 
 
 class ChaseError(RuntimeError):
@@ -110,6 +111,7 @@ def lib():
         L.chase_qr_prec.argtypes = [P, i, i, i, P, i, d, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.chase_cond_est.argtypes = [i, i, P, P, d, d, d, d, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.chase_filter_noalloc.argtypes = [i, i, P, i, i, P, i, P, d, d, d, P, i, P]
+        L.chase_selftest_wait_timeout.argtypes = [P, d]
         L.chase_status_string.argtypes = [i]
         L.chase_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -269,6 +271,12 @@ def chase_qr(h, X, est_cond, qr_force=0, check=True, prec=None):
     if check and rc not in (CHASE_OK, CHASE_CHOL_FAILED):
         raise ChaseError(rc, "chase_qr")
     return rc, v.value, info.value
+
+
+def chase_selftest_wait_timeout(h, seconds=0.01):
+    """Runs a device wait that nothing completes; returns the status the library reports
+    (CHASE_ERR_TIMEOUT when the bounded wait ran out and was reported, as designed)."""
+    return lib().chase_selftest_wait_timeout(h.ptr, float(seconds))
 
 
 def chase_lanczos_bounds(h, A, V0, steps, ell):

@@ -125,6 +125,11 @@ int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowe
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
             DevStatus* dst, Scratch scr, Scratch tailbuf, int* launches);
 
+// ---- failure path of the bounded device waits (selftest.cu) ----------------
+// One thread waits (at most `seconds`) on an mbarrier nothing arrives on and sets
+// dst->timeout, as the kernels do when a wait runs out.
+int selftest_wait_timeout(cudaStream_t st, double seconds, DevStatus* dst, int* launches);
+
 // ---- Lanczos spectral bounds (lanczos.cu) ----------------------------------
 // out = {lambda1, lambda_ell, b_sup} from nruns runs of m steps started at V0's columns.
 template <class T>

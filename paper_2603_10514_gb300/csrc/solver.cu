@@ -1215,6 +1215,21 @@ int chase_cond_est(int ell, int nlocked, const double* ritz, const int* degrees,
   return CHASE_OK;
 }
 
+int chase_selftest_wait_timeout(chase_handle h, double seconds) {
+  if (!h) return -1;
+  if (!(seconds > 0.0) || seconds > 10.0) return -2;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  cudaStream_t st = h->stream;
+  CHASE_CUDA_TRY(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), st));
+  TRY(selftest_wait_timeout(st, seconds, h->dstat, &h->launches));
+  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  const int timed_out = h->hstat->timeout;
+  CHASE_CUDA_TRY(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), st));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  return timed_out ? CHASE_ERR_TIMEOUT : CHASE_OK;
+}
+
 const char* chase_status_string(int status) {
   if (status < 0) return "invalid argument";
   switch (status) {

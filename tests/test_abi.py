@@ -77,6 +77,7 @@ def test_workspace_bytes_and_argument_checks(cl):
     # argument validation happens before any device work
     assert L.chase_solve(None, 0, 10, None, 10, 2, 1, None, None, None, 10, None, None, None, None, 0) == -1
     assert L.chase_qr(None, 0, 10, 2, None, 10, 1.0, 0, None, None) == -1
+    assert L.chase_selftest_wait_timeout(None, 0.01) == -1
 
 
 def test_cond_est_matches_oracle(cl):
