@@ -1,6 +1,7 @@
 """Failure detection on the GPU without a fault: a bounded device wait that runs out is
 reported to the host as CHASE_ERR_TIMEOUT, promptly, and the handle and the CUDA context
-stay usable afterwards (a filter on the same handle still matches the oracle)."""
+stay usable afterwards (a filter on the same handle still matches the oracle).  Collected
+after the parity suites (only tests/test_zz_no_alloc.py comes later)."""
 import time
 
 import numpy as np
