@@ -99,7 +99,11 @@ typedef struct {
    * of Y while the filter's gains are <= 1, so kappa_2([Y V]) can exceed Eq. full-est
    * (measured: up to ~10x); |rho_1|^{m_ell} bounds 1 / (smallest gain). */
   int cond_est_mode;
-  int reserved[5];
+  /* 1: each FP64_EMU filter call of chase_solve is recorded into a CUDA graph and launched
+     as one unit (the handle's stream must not be a default stream; otherwise the launches
+     are issued directly).  Default 0. */
+  int graph_filter;
+  int reserved[4];
 } chase_config;
 
 /* Spectral information the filter needs (Algorithm 1, step "estimate lambda_1,

@@ -47,7 +47,8 @@ class Config(ctypes.Structure):
                 ("eta", ctypes.c_double), ("cond_hi", ctypes.c_double), ("cond_lo", ctypes.c_double),
                 ("qr_force", ctypes.c_int), ("prec", ctypes.c_int), ("mp_switch", ctypes.c_double),
                 ("filtered_hook", ctypes.c_void_p), ("filtered_hook_ctx", ctypes.c_void_p),
-                ("cond_est_mode", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("cond_est_mode", ctypes.c_int), ("graph_filter", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 FILTERED_HOOK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,

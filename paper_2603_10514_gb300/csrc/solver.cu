@@ -36,7 +36,9 @@ using namespace chase;
 struct LaunchTimer {
   std::vector<cudaEvent_t> ev;
   size_t used = 0;
+  bool enabled = true;  // off while a stream is being captured into a graph
   void begin(cudaStream_t st) {
+    if (!enabled) return;
     while (ev.size() < used + 2) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -45,7 +47,7 @@ struct LaunchTimer {
     cudaEventRecord(ev[used], st);
   }
   void end(cudaStream_t st) {
-    if (ev.size() < used + 2) return;
+    if (!enabled || ev.size() < used + 2) return;
     cudaEventRecord(ev[used + 1], st);
     used += 2;
   }
@@ -343,10 +345,11 @@ OzBufs oz_carve(char* base, int n, int ncols) {
   return B;
 }
 
+// Enqueues the whole filter (no host synchronisation: it can be captured into a graph).
 template <class T>
-int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols, T* V, int ldv,
-              const int* deg, double c, double e, double lambda1, OzBufs& B, Scratch scr,
-              double* flops, int* steps) {
+int filter_oz_enqueue(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols, T* V,
+                      int ldv, const int* deg, double c, double e, double lambda1, OzBufs& B,
+                      Scratch scr, double* flops, int* steps) {
   cudaStream_t st = h->stream;
   if (ncols <= 0) return 0;
   const int M = B.M, kp = B.kp;
@@ -389,10 +392,64 @@ int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols,
     TRY(tc_unstack_V<T>(st, n, a, b, B.V64[deg[a] % 2], kp, V, ldv, &h->launches));
     a = b;
   }
-  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  return 0;
+}
+
+// Reads the device status word after the filter's work.
+inline int filter_finish(chase_ctx* h) {
+  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                                 h->stream));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(h->stream));
   if (h->hstat->timeout) return CHASE_ERR_TIMEOUT;
   return 0;
+}
+
+template <class T>
+int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols, T* V, int ldv,
+              const int* deg, double c, double e, double lambda1, OzBufs& B, Scratch scr,
+              double* flops, int* steps) {
+  if (ncols <= 0) return 0;
+  TRY(filter_oz_enqueue<T>(h, n, A, lda, split_A, ncols, V, ldv, deg, c, e, lambda1, B, scr, flops,
+                           steps));
+  return filter_finish(h);
+}
+
+// The same filter recorded into a CUDA graph and launched as one unit (the launch sequence of
+// a filter call is fixed by its degrees).  Needs a stream that can be captured (not one of
+// the default streams); otherwise the launches are issued directly.  Product launch times
+// are not taken per launch inside a graph.
+template <class T>
+int filter_oz_graph(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols, T* V,
+                    int ldv, const int* deg, double c, double e, double lambda1, OzBufs& B,
+                    Scratch scr, double* flops, int* steps) {
+  cudaStream_t st = h->stream;
+  if (ncols <= 0) return 0;
+  if ((uintptr_t)st <= 2)  // NULL, cudaStreamLegacy, cudaStreamPerThread: not capturable
+    return filter_oz<T>(h, n, A, lda, split_A, ncols, V, ldv, deg, c, e, lambda1, B, scr, flops,
+                        steps);
+  CHASE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  h->product_timer.enabled = false;
+  const int rc = filter_oz_enqueue<T>(h, n, A, lda, split_A, ncols, V, ldv, deg, c, e, lambda1, B,
+                                      scr, flops, steps);
+  h->product_timer.enabled = true;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(st, &g);
+  if (rc || ce != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? rc : CHASE_ERR_CUDA;
+  }
+  cudaGraphExec_t ge = nullptr;
+  if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return CHASE_ERR_CUDA;
+  }
+  const cudaError_t le = cudaGraphLaunch(ge, st);
+  const int frc = (le == cudaSuccess) ? filter_finish(h) : CHASE_ERR_CUDA;
+  cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  return frc;
 }
 
 // AQ = A Q (n x nu, both ld n) by the Ozaki-scheme product; A's planes must be ready.
@@ -711,10 +768,19 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       S.filter_flops_lowprec += fl;
       ++S.n_lowprec_iters;
     } else if (emu) {
-      rc = filter_oz<T>(h, n, A, lda, !A_oz, nu, V + (size_t)k * n, n, deg.data() + k, c, e, mu1,
-                        ozb, scr, &S.filter_flops, &S.filter_launches);
+      if (cfg.graph_filter) {
+        double tf = 0.0;
+        rc = filter_oz_graph<T>(h, n, A, lda, !A_oz, nu, V + (size_t)k * n, n, deg.data() + k, c,
+                                e, mu1, ozb, scr, &S.filter_flops, &S.filter_launches);
+        phase_end(tf);
+        S.t_filter += tf;
+        if ((uintptr_t)st > 2) S.t_filter_product += tf;  // no per-launch times inside a graph
+      } else {
+        rc = filter_oz<T>(h, n, A, lda, !A_oz, nu, V + (size_t)k * n, n, deg.data() + k, c, e, mu1,
+                          ozb, scr, &S.filter_flops, &S.filter_launches);
+        phase_end(S.t_filter);
+      }
       A_oz = true;
-      phase_end(S.t_filter);
     } else {
       rc = filter_inplace<T>(h, n, A, lda, nu, V + (size_t)k * n, n, P, n, deg.data() + k, c, e,
                              mu1, scr, &S.filter_flops, &S.filter_launches);
@@ -1097,7 +1163,7 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
   if (cfg) c = *cfg; else chase_config_default(&c);
   if (!(c.tol > 0.0) || c.max_iter < 0 || c.deg_init < 1 || c.deg_min < 1 || c.deg_max < c.deg_min ||
       !(c.eta > 0.0) || c.qr_force < 0 || c.qr_force > 4 || c.cond_est_mode < 0 ||
-      c.cond_est_mode > 1)
+      c.cond_est_mode > 1 || c.graph_filter < 0 || c.graph_filter > 1)
     return -8;
   if (c.prec != CHASE_FP64 && c.prec != CHASE_BF16X3 && c.prec != CHASE_FP64_EMU)
     return CHASE_ERR_UNSUPPORTED;

@@ -100,3 +100,35 @@ def test_cond_est_matches_oracle(cl):
 def test_cond_est_overflow_stays_finite_in_log(cl):
     est, lest = cl.chase_cond_est([-100.0, -1.0], [36, 2000], 0, -100.0, 1.0, 0.5)
     assert math.isinf(est) and math.isfinite(lest) and lest > 700
+
+
+def test_struct_layouts_match_the_header(cl, tmp_path):
+    """The binding's ctypes structures have the size and field offsets of the C header's
+    (compiled here with gcc), so every field reaches the library where it expects it."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"chase_config": cl.Config, "chase_stats": cl.Stats, "chase_iter_log": cl.IterLog,
+               "chase_bounds": cl.Bounds}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "chase_gb300.h"',
+             "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(cl.LIB_PATH), "..", "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
