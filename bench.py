@@ -436,7 +436,8 @@ def run_reference(args, rank):
     import workloads as W
     prob = W.c2_complex_clustered(n=args.n, nev=args.nev, nex=args.nex, seed=2)
     A = W.known_spectrum_matrix(prob.lam, prob.seed, prob.complex_, device="cpu").numpy()
-    mv = REF_MATVECS_PER_SOLVE or _estimate_matvecs(prob)
+    default = (prob.n, prob.nev, prob.nex) == (10000, 500, 100)
+    mv = REF_MATVECS_PER_SOLVE if default else _estimate_matvecs(prob)
     for _ in range(args.warmup):
         oracle_sample(A, prob, max(1, args.cpu_sample_cols // 4), deg=1)
     times = []
