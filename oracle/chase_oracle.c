@@ -485,7 +485,8 @@ int orc_jacobi_svd(int n, int l, const cplx* X, int ldx, double* sv) {
  *   b_sup       = max over runs of (theta_max + |beta_m|)     (an upper bound of lambda_n)
  *   lambda1     = min over runs of theta_min
  *   lambda_ell  = the smallest pooled Ritz value at which the spectral-density
- *                 estimate  (n / nruns) sum_runs sum_{theta_i <= x} tau_i  reaches ell.
+ *                 estimate  (n / nruns) sum_runs sum_{theta_i <= x} tau_i  reaches ell
+ *                 (to within a relative 1e-10, the rounding of the sum).
  * Outputs the three numbers in out[0..2] and every run's Ritz values in ritz
  * (nruns x m, may be NULL).
  */
@@ -549,10 +550,13 @@ int orc_lanczos_bounds(int n, const cplx* A, int lda, int nruns, const cplx* V0,
     while (j >= 0 && th[ord[j]] > th[k]) { ord[j + 1] = ord[j]; --j; }
     ord[j + 1] = k;
   }
+  /* "reaches ell" up to the rounding of the weights and of their sum: when the start
+   * vectors are orthonormal and the runs span the space, every eigenvalue's weights sum
+   * to exactly 1 and the estimate hits the integer ell at the last copy of lambda_ell */
   double cum = 0.0, lell = th[ord[tot - 1]];
   for (int i = 0; i < tot; ++i) {
     cum += tau[ord[i]] * (double)n / (double)nruns;
-    if (cum >= (double)ell) { lell = th[ord[i]]; break; }
+    if (cum >= (double)ell * (1.0 - 1e-10)) { lell = th[ord[i]]; break; }
   }
   if (lell < l1) lell = l1;
   out[0] = l1;

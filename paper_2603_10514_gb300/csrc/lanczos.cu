@@ -203,7 +203,7 @@ int lanczos_bounds(cudaStream_t st, int n, const T* A, int lda, int nruns, const
   double cum = 0.0, lell = hth[ord.back()];
   for (int idx : ord) {
     cum += htau[idx] * (double)n / (double)nruns;
-    if (cum >= (double)ell) { lell = hth[idx]; break; }
+    if (cum >= (double)ell * (1.0 - 1e-10)) { lell = hth[idx]; break; }  // up to rounding
   }
   out[0] = l1;
   out[1] = std::max(lell, l1);

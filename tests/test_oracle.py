@@ -519,6 +519,27 @@ def test_lanczos_full_length_reproduces_the_spectrum():
     assert ritz.min() >= lam[0] - 1e-12 and ritz.max() <= lam[-1] + 1e-12
 
 
+@pytest.mark.parametrize("complex_", [False, True])
+@pytest.mark.parametrize("n,seed", [(12, 8), (16, 9), (14, 21)])
+def test_lanczos_density_estimate_counts_eigenvalues_exactly(complex_, n, seed):
+    """Pins the lambda_ell output.  With nruns = n full-length runs started at the columns
+    of the identity, every run's Ritz values are the eigenvalues and its weight on
+    eigenvalue lambda_k is tau = |u_k[r]|^2 (the squared r-th component of the unit
+    eigenvector u_k).  Summed over the runs these weights are ||u_k||^2 = 1, and the scale
+    n / nruns is 1, so the spectral-density estimate is the exact eigenvalue count: it
+    reaches ell at lambda_ell for EVERY ell = 1..n (brute force against eigvalsh).  A weight
+    taken from another component of the tridiagonal's eigenvector, or another scale than
+    n / nruns, moves lambda_ell off the ell-th eigenvalue."""
+    G = W.gaussian((n, n), seed, complex_)
+    A = 0.5 * (G + G.conj().T)
+    lam = np.linalg.eigvalsh(A)
+    V = np.eye(n, dtype=np.complex128 if complex_ else np.float64)
+    for ell in range(1, n + 1):
+        (l1, lell, bsup), ritz = oracle.lanczos_bounds(A, V, n, ell)
+        assert abs(lell - lam[ell - 1]) <= 1e-9 * max(1.0, abs(lam).max()), (ell, lell, lam[ell - 1])
+        assert abs(l1 - lam[0]) <= 1e-9 * max(1.0, abs(lam).max())
+
+
 @pytest.mark.parametrize("opt", [False, True])
 def test_condition_estimate_against_exact_kappa_per_iteration(opt):
     """Figure 2's comparison on a synthetic spectrum, exact kappa_2 of [Y V] from the oracle's
