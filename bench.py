@@ -51,10 +51,10 @@ BF16_PEAK_TFLOPS, BF16_SUSTAINED_TFLOPS = _measured_peaks()
 # pairs (i, j) with i + j <= 8.
 OZAKI_PAIRS = 28
 # DRAM bytes (read + write) of one Ozaki product (tail + exact-level kernel) of the default
-# workload (complex n = 10000, 600 active columns), from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass): tail 6.83 GB + 0.097 GB, exact
-# 4.63 GB + 0.094 GB; profiles/oz_part_kernel_fp64_emu_n10000.md.  Launches with fewer active
-# columns read the same digit planes of A, which are most of it.
+# workload (complex n = 10000, 600 active columns), measured by one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass): tail kernel 6.83 GB read and
+# 0.097 GB written, exact-level kernel 4.63 GB read and 0.094 GB written.  Launches with
+# fewer active columns read the same digit planes of A, which are most of it.
 OZ_TRAFFIC_PER_LAUNCH = 6.83e9 + 0.097e9 + 4.63e9 + 0.094e9
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
@@ -427,8 +427,44 @@ def run_serve(args):
                       "max_in_flight": inflight}), flush=True)
 
 
+def oracle_full_solve_c1():
+    """One complete oracle solve (Algorithm 1, every step) of the small real workload
+    (n = 1000, nev 20, nex 10, fixed degree 20): the measured anchor of the extrapolated
+    CPU baseline.  Returns seconds, column MatVecs (filter + Rayleigh-Ritz / residual
+    products) and the status."""
+    import oracle
+    import workloads as W
+    prob = W.c1_real_small()
+    A = W.known_spectrum_matrix(prob.lam, prob.seed, False, device="cpu").numpy()
+    V0 = W.start_block(prob.n, prob.ell, prob.seed, False)
+    l1, le, bs = prob.bounds
+    oracle.lib()
+    t0 = time.perf_counter()
+    r = oracle.solve(A, V0, prob.nev, prob.nex, opt_degree=False, deg_init=prob.deg_init,
+                     lambda1=l1, lambda_ell=le, b_sup=bs)
+    dt = time.perf_counter() - t0
+    mv = r["summary"]["matvecs"] + 2 * sum(prob.ell - g["locked_before"] for g in r["logs"])
+    return dt, mv, r["status"], prob.n
+
+
+def cpu_anchor(per_mv_c2, n_c2):
+    """The C1 full solve timed and set beside the C2 sample: the oracle computes in complex
+    arithmetic whatever the input type, so a column MatVec costs ~n^2 work at any size and the
+    C1 per-MatVec time scaled by (n_C2 / n_C1)^2 predicts the C2 sample's."""
+    dt, mv, status, n1 = oracle_full_solve_c1()
+    per_mv_c1 = dt / mv
+    return {"workload": "real symmetric n=%d, nev 20, nex 10, degree 20 (complete oracle solve)" % n1,
+            "solve_s": dt, "status": status, "column_matvecs": mv, "s_per_matvec": per_mv_c1,
+            "s_per_matvec_scaled_to_n%d" % n_c2: per_mv_c1 * (n_c2 / n1) ** 2,
+            "s_per_matvec_sampled_at_n%d" % n_c2: per_mv_c2}
+
+
 def run_reference(args, rank):
-    """The oracle arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    """The oracle arm: the CPU oracle timed on the host cores (rank 0 only).  A complete
+    oracle solve of this workload takes hours, so each step times a bounded sample of it
+    (the oracle's filter on a few columns of the same matrix); `ms_per_step` is the measured
+    time of that sample and `value` the solves/s it implies for a whole solve (the sample's
+    time per column MatVec times the MatVecs of a solve)."""
     if rank != 0:
         return
     import numpy as np
@@ -440,21 +476,26 @@ def run_reference(args, rank):
     mv = REF_MATVECS_PER_SOLVE if default else _estimate_matvecs(prob)
     for _ in range(args.warmup):
         oracle_sample(A, prob, max(1, args.cpu_sample_cols // 4), deg=1)
-    times = []
+    per_mv, sample_s = [], []
     for _ in range(args.steps):
-        per_mv, _ = oracle_sample(A, prob, args.cpu_sample_cols)
-        times.append(per_mv * mv)
-    t = statistics.mean(times)
+        pm, dt = oracle_sample(A, prob, args.cpu_sample_cols)
+        per_mv.append(pm)
+        sample_s.append(dt)
+    t_solve = statistics.mean(per_mv) * mv
     cores = os.cpu_count()
-    value = 1.0 / t
+    value = 1.0 / t_solve
+    sample = ("each step: the oracle's filter on %d columns x degree 2 of the n=%d matrix "
+              "(%.1f s measured); solves/s = 1 / (its time per column MatVec x %d column MatVecs "
+              "per solve)" % (args.cpu_sample_cols, prob.n, statistics.mean(sample_s), mv))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(sample_s) * 1e3, "ms_per_solve_extrapolated": t_solve * 1e3,
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
         "config": _config(args, prob),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": "oracle filter on %d columns x degree 2 of the n=%d matrix per step, "
-                                   "scaled by %d column MatVecs per solve" % (args.cpu_sample_cols, prob.n, mv)},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -552,30 +593,48 @@ def main():
     rc, ev, res, st, logs = results[-1]
     launches = sum(r[3]["kernel_launches"] for r in results)
     # roofline of the dominant kernel: the filter product (CUDA events around each product
-    # launch on the handle's stream, summed by the library, divided by the launch count)
+    # launch on the handle's stream, summed by the library, divided by the launch count).
+    # achieved = the method's algorithmic work (column MatVecs x 8 n^2 complex / 2 n^2 real
+    # flops, FP64) per launch / the launch's duration.
     nl = max(1, st["filter_launches"])
     dur_launch = st["t_filter_product"] / nl
+    fl_launch = st["filter_flops"] / nl
+    achieved = fl_launch / dur_launch / 1e12 if dur_launch > 0 else None
+    # algorithmic DRAM bytes of one full-width product: A once (16 n^2 complex / 8 n^2 real)
+    # plus V_{i-1}, V_{i-2} read and V_i written (3 x 16 n ell)
+    esz = 16 if prob.complex_ else 8
+    alg_bytes = esz * n * n + 3 * esz * n * l
     if args.prec == "fp64":
-        fl_launch = st["filter_flops"] / nl
-        achieved = fl_launch / dur_launch / 1e12 if dur_launch > 0 else None
         roof = {"kernel": "gemm_kernel (FP64 DFMA filter product, fused three-term epilogue)",
                 "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz", "traffic": None}
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz", "traffic": None,
+                "algorithmic_bytes": alg_bytes}
     else:
-        # BF16 tensor work: OZAKI_PAIRS digit products per FP64-equivalent flop for the Ozaki
-        # product, 3 for the BF16x3 filter iterations
+        # the FP64-accurate products run on the BF16 tensor cores: the method's FP64 work is
+        # set against the BF16 pipe's measured sustained peak (frac), and the BF16 digit
+        # products the kernels actually issue (OZAKI_PAIRS per FP64-equivalent flop; 3 for the
+        # BF16x3 filter iterations) give the tensor pipe's own efficiency (frac_tensor_pipe)
         lp = st["filter_flops_lowprec"]
         tc_flops = OZAKI_PAIRS * (st["filter_flops"] - lp) + 3.0 * lp
-        achieved = tc_flops / nl / dur_launch / 1e12 if dur_launch > 0 else None
+        pipe = tc_flops / nl / dur_launch / 1e12 if dur_launch > 0 else None
+        traffic = (OZ_TRAFFIC_PER_LAUNCH if (lp == 0 and args.n == 10000 and
+                                             args.prec == "fp64_emu") else None)
         roof = {"kernel": "oz_part_kernel tail + exact levels (Ozaki-scheme FP64 product on "
                           "BF16 tcgen05)" +
                           (" + tc_filter_bf16x3_kernel" if lp > 0 else ""),
                 "bound": "tensor", "achieved": achieved, "peak": BF16_SUSTAINED_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / BF16_SUSTAINED_TFLOPS if achieved else None,
+                "achieved_meaning": "FP64-equivalent flops of the method (column MatVecs x 8 n^2) "
+                                    "per product launch / its CUDA-event duration",
                 "peak_source": "measured: cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
-                "traffic": (OZ_TRAFFIC_PER_LAUNCH if (lp == 0 and args.n == 10000 and
-                                                      args.prec == "fp64_emu") else None)}
+                "tensor_pipe_tflops": pipe,
+                "frac_tensor_pipe": pipe / BF16_SUSTAINED_TFLOPS if pipe else None,
+                "tensor_pipe_meaning": "BF16 digit products issued (%d per FP64-equivalent flop) "
+                                       "per launch / duration" % OZAKI_PAIRS,
+                "vs_fp64_dfma_peak": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "traffic": traffic, "algorithmic_bytes": alg_bytes,
+                "traffic_vs_algorithmic": traffic / alg_bytes if traffic else None}
     fp64_equiv = st["filter_flops"] / st["t_filter"] / 1e12 if st["t_filter"] > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -641,7 +700,8 @@ def main():
             "value": 1.0 / t_cpu, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": "oracle filter (plain C FP64, OpenMP) on %d columns x degree 2 of the same A, "
                       "%.1f s; scaled by the %d column MatVecs of the GPU solve (filter + RR + "
-                      "residual products; QR and Jacobi not counted)" % (args.cpu_sample_cols, dt, mv_solve)}
+                      "residual products; QR and Jacobi not counted)" % (args.cpu_sample_cols, dt, mv_solve),
+            "measured_anchor": cpu_anchor(per_mv, n)}
     h.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -99,9 +99,10 @@ typedef struct {
    * of Y while the filter's gains are <= 1, so kappa_2([Y V]) can exceed Eq. full-est
    * (measured: up to ~10x); |rho_1|^{m_ell} bounds 1 / (smallest gain). */
   int cond_est_mode;
-  /* 1: each FP64_EMU filter call of chase_solve is recorded into a CUDA graph and launched
-     as one unit (the handle's stream must not be a default stream; otherwise the launches
-     are issued directly).  Default 0. */
+  /* 1: each FP64_EMU filter call of chase_solve is recorded into a CUDA graph (stream
+     capture, thread-local mode) and launched as one unit; the handle's stream must not be
+     a default stream (NULL, cudaStreamLegacy, cudaStreamPerThread), otherwise the launches
+     are issued directly.  Same kernels in the same order: results are identical.  Default 0. */
   int graph_filter;
   int reserved[4];
 } chase_config;
@@ -129,7 +130,10 @@ typedef struct {
   double t_rr_eig;         /* part of t_rr spent in the Jacobi eigensolver */
   int jacobi_sweeps;       /* Jacobi sweeps summed over iterations */
   double t_filter_product; /* part of t_filter spent in the product kernels alone (CUDA events
-                              around each launch) */
+                              around each launch; filters launched as graphs add nothing) */
+  double t_graph_build;    /* graph_filter = 1: host seconds spent recording and instantiating
+                              the filter graphs (inside t_filter) */
+  int graph_launches;      /* graph_filter = 1: filter calls that ran as one graph launch */
 } chase_stats;
 
 /* Per-iteration record (the kind of data Figure 2 plots). */
@@ -192,7 +196,8 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
  * [c - e, c + e] (e > 0) and lambda1 < c - e.
  *   degrees   host, ncols ints, ascending, each >= 0 (0 copies the column).
  *   dV        device n x ncols input (not modified); dVout device n x ncols
- *             output (may equal dV).
+ *             output: either dV itself with ldvout == ldv (filtered in place) or a
+ *             block that overlaps neither dV nor dA (otherwise -14, nothing done).
  *   prec      CHASE_FP64, CHASE_FP64_EMU (Ozaki-scheme FP64 products on the
  *             tensor cores) or CHASE_BF16X3 (each A*V product as three BF16
  *             tensor-core products of hi/lo splits, FP32 accumulation); the
@@ -298,11 +303,13 @@ int chase_selftest_wait_timeout(chase_handle h, double seconds);
  * one file-scope device array of CHASE_FILTER_NOALLOC_MAX_BYTES that every GPU
  * loading the library holds until the process exits.
  *
- * Arguments as chase_filter (FP64 only), without a handle: the work is ordered
+ * Arguments as chase_filter (FP64 only), without a handle (dVout: dV itself with
+ * ldvout == ldv, or clear of dV and dA; otherwise -12): the work is ordered
  * on `cuda_stream` (a cudaStream_t, NULL = legacy default stream) of the
  * current device, and the call returns after it completes; while `cuda_stream`
  * is being captured into a CUDA graph the work is recorded and the call returns
- * at once (replaying the graph runs the filter on the captured pointers).  The
+ * at once (replaying the graph runs the filter on the captured pointers; a capture
+ * that was already invalidated gives CHASE_ERR_CUDA).  The
  * caller passes and owns dV and dVout as before.
  * Limits and behaviour:
  *   - sizeof(element) * n * ncols must be <= CHASE_FILTER_NOALLOC_MAX_BYTES,

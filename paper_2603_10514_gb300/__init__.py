@@ -68,7 +68,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int), ("filter_launches", ctypes.c_int),
                 ("n_lowprec_iters", ctypes.c_int), ("t_filter_lowprec", ctypes.c_double),
                 ("filter_flops_lowprec", ctypes.c_double), ("t_rr_eig", ctypes.c_double),
-                ("jacobi_sweeps", ctypes.c_int), ("t_filter_product", ctypes.c_double)]
+                ("jacobi_sweeps", ctypes.c_int), ("t_filter_product", ctypes.c_double),
+                ("t_graph_build", ctypes.c_double), ("graph_launches", ctypes.c_int)]
 
 
 class IterLog(ctypes.Structure):

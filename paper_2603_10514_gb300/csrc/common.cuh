@@ -73,6 +73,24 @@ constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Byte range [lo, hi) a column-major n x ncols block with leading dimension ld occupies.
+inline bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+  return a0 < b0 + bbytes && b0 < a0 + abytes;
+}
+inline size_t block_bytes(int n, int ncols, int ld, size_t elem) {
+  return ncols > 0 ? elem * ((size_t)ld * (size_t)(ncols - 1) + (size_t)n) : 0;
+}
+// The filters write their result block `out` while they still read `in` and A: `out` must
+// be `in` itself (same leading dimension: the in-place filter) or lie clear of both.
+inline bool output_placement_ok(const void* out, int ldo, const void* in, int ldi, const void* A,
+                                int lda, int n, int ncols, size_t elem) {
+  const size_t ob = block_bytes(n, ncols, ldo, elem);
+  if (ranges_overlap(out, ob, A, block_bytes(n, n, lda, elem))) return false;
+  if (out == in) return ldo == ldi;
+  return !ranges_overlap(out, ob, in, block_bytes(n, ncols, ldi, elem));
+}
+
 // Device status word written by kernels that can fail without trapping.
 struct DevStatus {
   int chol_info;    // first non-positive pivot + 1 (0 = success)

@@ -117,11 +117,13 @@ int run(cudaStream_t st, void* base, int n, const T* A, int lda, int ncols, cons
   }
   int rc = filter_fixed_scratch<T>(st, n, A, lda, ncols, out, ldo, P, deg, c, e, lambda1, scr);
   if (rc) return rc;
-  // while the stream is captured into a graph the work is only recorded: return at once
+  // while the stream is captured into a graph the work is only recorded: return at once.
+  // A capture that has been invalidated recorded nothing and runs nothing: report it.
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return CHASE_ERR_CUDA;
-  if (cs == cudaStreamCaptureStatusNone && cudaStreamSynchronize(st) != cudaSuccess)
-    return CHASE_ERR_CUDA;
+  if (cs == cudaStreamCaptureStatusActive) return CHASE_OK;
+  if (cs != cudaStreamCaptureStatusNone) return CHASE_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CHASE_ERR_CUDA;
   return CHASE_OK;
 }
 
@@ -147,6 +149,7 @@ extern "C" int chase_filter_noalloc(chase_dtype dtype, int n, const void* dA, in
   if (ldvout < n) return -13;
   if (ncols == 0) return CHASE_OK;
   const size_t elem = (dtype == CHASE_R64) ? sizeof(double) : 2 * sizeof(double);
+  if (!chase::output_placement_ok(dVout, ldvout, dV, ldv, dA, lda, n, ncols, elem)) return -12;
   if (elem * (size_t)n * (size_t)ncols > kNoAllocScratchBytes) return CHASE_ERR_TOO_LARGE;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return CHASE_ERR_CUDA;

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -418,15 +419,19 @@ int filter_oz(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols,
 // a filter call is fixed by its degrees).  Needs a stream that can be captured (not one of
 // the default streams); otherwise the launches are issued directly.  Product launch times
 // are not taken per launch inside a graph.
+// *t_build receives the host time spent recording and instantiating the graph (seconds);
+// *launched is set when the filter ran as a graph.
 template <class T>
 int filter_oz_graph(chase_ctx* h, int n, const T* A, int lda, bool split_A, int ncols, T* V,
                     int ldv, const int* deg, double c, double e, double lambda1, OzBufs& B,
-                    Scratch scr, double* flops, int* steps) {
+                    Scratch scr, double* flops, int* steps, double* t_build, bool* launched) {
   cudaStream_t st = h->stream;
+  *launched = false;
   if (ncols <= 0) return 0;
   if ((uintptr_t)st <= 2)  // NULL, cudaStreamLegacy, cudaStreamPerThread: not capturable
     return filter_oz<T>(h, n, A, lda, split_A, ncols, V, ldv, deg, c, e, lambda1, B, scr, flops,
                         steps);
+  const auto tb0 = std::chrono::steady_clock::now();
   CHASE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   h->product_timer.enabled = false;
   const int rc = filter_oz_enqueue<T>(h, n, A, lda, split_A, ncols, V, ldv, deg, c, e, lambda1, B,
@@ -445,6 +450,8 @@ int filter_oz_graph(chase_ctx* h, int n, const T* A, int lda, bool split_A, int 
     cudaGetLastError();
     return CHASE_ERR_CUDA;
   }
+  *t_build += std::chrono::duration<double>(std::chrono::steady_clock::now() - tb0).count();
+  *launched = true;
   const cudaError_t le = cudaGraphLaunch(ge, st);
   const int frc = (le == cudaSuccess) ? filter_finish(h) : CHASE_ERR_CUDA;
   cudaGraphExecDestroy(ge);
@@ -769,12 +776,15 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       ++S.n_lowprec_iters;
     } else if (emu) {
       if (cfg.graph_filter) {
-        double tf = 0.0;
+        // t_filter covers recording, instantiation, launch and completion; the recording
+        // and instantiation alone go to t_graph_build.  The product launches inside a graph
+        // are not timed one by one, so t_filter_product gets nothing from such a filter.
+        bool launched = false;
         rc = filter_oz_graph<T>(h, n, A, lda, !A_oz, nu, V + (size_t)k * n, n, deg.data() + k, c,
-                                e, mu1, ozb, scr, &S.filter_flops, &S.filter_launches);
-        phase_end(tf);
-        S.t_filter += tf;
-        if ((uintptr_t)st > 2) S.t_filter_product += tf;  // no per-launch times inside a graph
+                                e, mu1, ozb, scr, &S.filter_flops, &S.filter_launches,
+                                &S.t_graph_build, &launched);
+        phase_end(S.t_filter);
+        if (launched) ++S.graph_launches;
       } else {
         rc = filter_oz<T>(h, n, A, lda, !A_oz, nu, V + (size_t)k * n, n, deg.data() + k, c, e, mu1,
                           ozb, scr, &S.filter_flops, &S.filter_launches);
@@ -1215,6 +1225,10 @@ int chase_filter(chase_handle h, chase_dtype dtype, int n, const void* dA, int l
   if (ncols > 0 && !dVout) return -14;
   if (ldvout < n) return -15;
   if (ncols == 0) return CHASE_OK;
+  {
+    const size_t elem = (dtype == CHASE_R64) ? sizeof(double) : sizeof(z64);
+    if (!output_placement_ok(dVout, ldvout, dV, ldv, dA, lda, n, ncols, elem)) return -14;
+  }
   if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
   if (dtype == CHASE_R64)
     return filter_impl<double>(h, n, (const double*)dA, lda, ncols, (const double*)dV, ldv, degrees,

@@ -86,3 +86,44 @@ def test_full_size_solve_properties(cl, c2):
     R = A @ Ys - Ys * lam
     rn = torch.linalg.vector_norm(R, dim=0).cpu().numpy()
     assert rn.max() <= 1e-10 * normA, rn
+
+
+def test_mixed_precision_workload_full_size(cl, measurements):
+    """The mixed-precision workload at its full size: complex Hermitian n = 20000, nev 1000,
+    nex 200, the clustered spectrum.  The BF16x3 filter (while the residuals are large, then
+    FP64-accurate products) and the FP64-emulated path both converge (residuals < tol) with
+    eigenvalues within 1e-10 ||A|| of the known spectrum and of each other; the two times
+    are reported in the terminal summary."""
+    prob = W.c2_complex_clustered(n=20000, nev=1000, nex=200, seed=3)
+    A = W.known_spectrum_matrix(prob.lam, prob.seed, True, device="cuda")
+    V0 = W.start_block(prob.n, prob.ell, prob.seed, True)
+    normA = np.abs(prob.lam).max()
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, prec in (("bf16x3", cl.CHASE_BF16X3), ("fp64_emu", cl.CHASE_FP64_EMU)):
+        h = cl.Handle(0, stream=stream.cuda_stream)
+        cfg = cl.config_default(opt_degree=1, deg_init=prob.deg_init, deg_min=prob.deg_min,
+                                deg_max=prob.deg_max, tol=prob.tol, prec=prec)
+        try:
+            V = dev(V0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, ev, res, st, _ = cl.chase_solve(h, A, V, prob.nev, prob.nex, prob.bounds, cfg)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        finally:
+            h.close()
+        del V
+        assert rc == 0, name
+        assert res.max() < prob.tol, name
+        err = float(np.abs(ev - prob.lam[:prob.nev]).max())
+        assert err <= 1e-10 * normA, (name, err)
+        out[name] = (ev, e0.elapsed_time(e1) / 1e3, st, err)
+    assert np.abs(out["bf16x3"][0] - out["fp64_emu"][0]).max() <= 1e-10 * normA
+    tb, tf = out["bf16x3"][1], out["fp64_emu"][1]
+    measurements.append(
+        "mixed-precision workload (complex n=20000, nev 1000, nex 200): bf16x3 %.2f s "
+        "(%d iterations, %d in BF16x3, max |dlambda| %.1e), fp64_emu %.2f s (%d iterations, "
+        "max |dlambda| %.1e), speed-up %.2fx"
+        % (tb, out["bf16x3"][2]["iterations"], out["bf16x3"][2]["n_lowprec_iters"], out["bf16x3"][3],
+           tf, out["fp64_emu"][2]["iterations"], out["fp64_emu"][3], tf / tb))

@@ -128,6 +128,41 @@ def test_solve_with_emulated_fp64_matches_oracle(cl, handle, prec_name):
         assert abs(st["matvecs"] - ref["summary"]["matvecs"]) <= 0.05 * ref["summary"]["matvecs"]
 
 
+def test_solve_with_graph_launched_filters(cl):
+    """chase_config.graph_filter = 1: every filter call of the solve is recorded into a
+    CUDA graph and launched as one unit on a handle with its own (capturable) stream.  The
+    graph runs the same kernels in the same order, so the results equal the directly
+    launched solve's bit for bit, and match the oracle; on torch's default stream (not
+    capturable) the option falls back to direct launches with the same results."""
+    prob = W.c2_complex_clustered(n=900, nev=30, nex=10, seed=18)
+    A_t = W.known_spectrum_matrix(prob.lam, prob.seed, True, device="cuda")
+    V0 = W.start_block(prob.n, prob.ell, prob.seed, True)
+    l1, le, bs = prob.bounds
+    ref = oracle.solve(A_t.cpu().numpy(), V0, prob.nev, prob.nex, opt_degree=True, lambda1=l1,
+                       lambda_ell=le, b_sup=bs)
+    normA = np.abs(prob.lam).max()
+    runs = {}
+    for name, stream, graph in (("direct", None, 0), ("graph", None, 1), ("legacy", 0, 1)):
+        h = cl.Handle(0, stream=stream)
+        try:
+            cfg = cl.config_default(opt_degree=1, prec=cl.CHASE_FP64_EMU, graph_filter=graph)
+            V = dev(V0)
+            rc, ev, res, st, _ = cl.chase_solve(h, A_t, V, prob.nev, prob.nex, prob.bounds, cfg)
+        finally:
+            h.close()
+        assert rc == 0, name
+        assert res.max() < prob.tol
+        assert np.abs(ev - ref["evals"]).max() <= 1e-10 * normA
+        runs[name] = (ev, res, V.cpu().numpy(), st)
+    assert runs["graph"][3]["graph_launches"] == runs["graph"][3]["iterations"]
+    assert runs["graph"][3]["t_graph_build"] > 0.0
+    assert runs["direct"][3]["graph_launches"] == 0 and runs["legacy"][3]["graph_launches"] == 0
+    for name in ("graph", "legacy"):
+        np.testing.assert_array_equal(runs[name][0], runs["direct"][0])
+        np.testing.assert_array_equal(runs[name][1], runs["direct"][1])
+        np.testing.assert_array_equal(runs[name][2], runs["direct"][2])
+
+
 # --------------------------------------------------------------------------
 # QR with emulated-FP64 block products (Gram X^H X and X R^{-1}, Algorithm 2)
 # --------------------------------------------------------------------------

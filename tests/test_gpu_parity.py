@@ -111,6 +111,22 @@ def test_filter_rejects_bad_arguments(cl, handle):
         cl.chase_filter(handle, A, V, [2, 3], 0.5, 0.6, 0.3)  # lambda1 inside the interval
 
 
+def test_filter_rejects_outputs_that_overlap_its_inputs(cl, handle):
+    """The filter reads its input block and A while it writes the output: an output that is
+    the input shifted by a column, or that lies inside A, is rejected (-14) before any device
+    work; the input block itself (same leading dimension) is the in-place filter."""
+    n = 32
+    A = dev(np.eye(n) * 0.1)
+    buf = dev(np.arange(n * 5, dtype=np.float64).reshape(5, n).T)  # n x 5
+    before = host(buf)
+    for out, V in ((buf[:, 1:4], buf[:, 0:3]), (A[:, 2:5], buf[:, 0:3])):
+        with pytest.raises(cl.ChaseError) as ex:
+            cl.chase_filter(handle, A, V, [1, 2, 3], 0.5, 0.6, -1.2, out=out)
+        assert ex.value.code == -14
+    np.testing.assert_array_equal(host(buf), before)
+    assert np.abs(host(A) - 0.1 * np.eye(n)).max() == 0.0
+
+
 # --------------------------------------------------------------------------
 # QR (Algorithms 2 and 3)
 # --------------------------------------------------------------------------

@@ -93,6 +93,20 @@ def test_noalloc_rejects_blocks_beyond_the_fixed_scratch(cl):
     assert bool((out == 7.0).all())
 
 
+def test_noalloc_rejects_outputs_that_overlap_its_inputs(cl):
+    """An output shifted against the input block, or inside A, would be overwritten while
+    the filter still reads it: rejected (-12) before any device work."""
+    n = 40
+    A = _dev(np.eye(n) * 0.1)
+    buf = _dev(np.arange(n * 6, dtype=np.float64).reshape(6, n).T)
+    before = buf.cpu().numpy()
+    for out, V in ((buf[:, 2:5], buf[:, 0:3]), (A[:, 1:4], buf[:, 0:3])):
+        with pytest.raises(cl.ChaseError) as ex:
+            cl.chase_filter_noalloc(A, V, [1, 2, 3], 0.5, 0.6, -1.2, out=out)
+        assert ex.value.code == -12
+    np.testing.assert_array_equal(buf.cpu().numpy(), before)
+
+
 def test_noalloc_filter_captures_into_a_cuda_graph(cl):
     """Recorded once into a CUDA graph (global capture mode: an allocation would fail the
     capture), replayed on new contents of the same input buffer: every replay matches
