@@ -47,15 +47,13 @@ def _measured_peaks():
 
 
 BF16_PEAK_TFLOPS, BF16_SUSTAINED_TFLOPS = _measured_peaks()
-# BF16 digit products per real FP64 product in the Ozaki-scheme kernel: 7 digits per operand,
-# pairs (i, j) with i + j <= 8.
-OZAKI_PAIRS = 28
-# DRAM bytes (read + write) of one Ozaki product (tail + exact-level kernel) of the default
-# workload (complex n = 10000, 600 active columns), measured by one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass): tail kernel 6.83 GB read and
-# 0.097 GB written, exact-level kernel 4.63 GB read and 0.094 GB written.  Launches with
-# fewer active columns read the same digit planes of A, which are most of it.
-OZ_TRAFFIC_PER_LAUNCH = 6.83e9 + 0.097e9 + 4.63e9 + 0.094e9
+# BF16 tensor-core products per real FP64 product in the emulated mode: one modular product
+# per modulus of the Ozaki scheme II (17 moduli <= 256).
+OZAKI_PAIRS = 17
+# DRAM bytes (read + write) of one emulated product of the default workload (complex
+# n = 10000, 600 active columns) from an ncu capture of the current kernels; None until the
+# capture of these kernels is taken (the line then reports traffic as null).
+OZ_TRAFFIC_PER_LAUNCH = None
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
@@ -142,7 +140,7 @@ def run_filter(args):
         line["frac_of_fp64_peak"] = flops / t / 1e12 / FP64_PEAK_TFLOPS
     else:
         # BF16 tensor-core products of the stacked real operator (2n x 2n) per step:
-        # 3 for BF16x3, OZAKI_PAIRS digit pairs for the Ozaki scheme
+        # 3 for BF16x3, OZAKI_PAIRS modular products for the Ozaki scheme II
         npairs = 3 if args.prec == "bf16x3" else OZAKI_PAIRS
         tc = npairs * 2.0 * (2 * n) * (2 * n) * k * args.degree / t / 1e12
         line["bf16_tensor_tflops"] = tc
@@ -620,8 +618,8 @@ def main():
         pipe = tc_flops / nl / dur_launch / 1e12 if dur_launch > 0 else None
         traffic = (OZ_TRAFFIC_PER_LAUNCH if (lp == 0 and args.n == 10000 and
                                              args.prec == "fp64_emu") else None)
-        roof = {"kernel": "oz_part_kernel tail + exact levels (Ozaki-scheme FP64 product on "
-                          "BF16 tcgen05)" +
+        roof = {"kernel": "ozm_kernel + crt_kernel (Ozaki scheme II FP64 product: 17 modular "
+                          "BF16 tcgen05 products, CRT reconstruction)" +
                           (" + tc_filter_bf16x3_kernel" if lp > 0 else ""),
                 "bound": "tensor", "achieved": achieved, "peak": BF16_SUSTAINED_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / BF16_SUSTAINED_TFLOPS if achieved else None,
@@ -630,7 +628,7 @@ def main():
                 "peak_source": "measured: cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
                 "tensor_pipe_tflops": pipe,
                 "frac_tensor_pipe": pipe / BF16_SUSTAINED_TFLOPS if pipe else None,
-                "tensor_pipe_meaning": "BF16 digit products issued (%d per FP64-equivalent flop) "
+                "tensor_pipe_meaning": "BF16 modular products issued (%d per FP64-equivalent flop) "
                                        "per launch / duration" % OZAKI_PAIRS,
                 "vs_fp64_dfma_peak": achieved / FP64_PEAK_TFLOPS if achieved else None,
                 "traffic": traffic, "algorithmic_bytes": alg_bytes,

@@ -45,10 +45,13 @@ typedef enum { CHASE_R64 = 0, CHASE_C128 = 1 } chase_dtype;
 /* Arithmetic of the block products.
  *   CHASE_FP64      native FP64 (DFMA) everywhere.
  *   CHASE_FP64_EMU  every block product (filter A*V, Rayleigh-Ritz A*Q, Q^H(AQ), QW,
- *                   (AQ)W, and the QR's Gram X^H X and X R^{-1}) by the Ozaki scheme
- *                   on the BF16 tensor cores: 7 signed 8-bit digits per operand entry,
- *                   exact integer accumulation of the leading levels, accurate to
- *                   ~2^-53 |A||V| per entry like an FP64 product.
+ *                   (AQ)W, and the QR's Gram X^H X and X R^{-1}) by the Ozaki scheme II
+ *                   on the BF16 tensor cores: operands rounded to 57-bit integers (one
+ *                   power-of-two scale per row / column), their product formed exactly
+ *                   from 17 modular BF16 products (moduli <= 256) and the Chinese
+ *                   remainder theorem, then rounded once to FP64; accurate to
+ *                   ~2^-57 K max|A_m.| max|V_.c| per entry, the class of an FP64 product
+ *                   (inner dimension up to 2^17: complex n <= 65536, real n <= 131072).
  *   CHASE_BF16X3    mixed: BF16x3 filter products (three BF16 tensor-core
  *                   products of hi/lo splits, FP32 accumulation) while the
  *                   residuals are large, then as CHASE_FP64_EMU.

@@ -1,55 +1,43 @@
 // gemm_oz.cu -- FP64-accurate dense products on the BF16 tensor cores by the
-// Ozaki scheme (Ozaki, Ogita, Oishi & Rump, "Error-free transformations of
-// matrix multiplication by using fast routines of matrix multiplication and its
-// applications", Numer. Algorithms 2012): the filter's A*V, the Rayleigh-Ritz
-// product A*Q and the block products of the QR and Rayleigh-Ritz steps.
+// Ozaki scheme II (Ozaki, Uchino & Imamura, "Ozaki Scheme II: A GEMM-oriented
+// emulation of floating-point matrix multiplication using an integer modular
+// technique", 2025): the filter's A*V, the Rayleigh-Ritz product A*Q and the
+// block products of the QR and Rayleigh-Ritz steps.
 //
-// Slicing.  Every row m of the (stacked real) left operand is scaled by 2^-e_m
-// so that its entries lie in (-1, 1), every column c of the right operand by
-// 2^-f_c, and each scaled entry is cut into S = 7 signed 8-bit digits by
-// rounding to nearest: x = sum_i d_i 2^{-8i} + O(2^-57), |d_1| <= 256,
-// |d_i| <= 128 (i > 1).  Then
-//   (A V)[m, c] = 2^{e_m + f_c} sum_{t=2}^{8} 2^{-8t} L_t[m, c],
-//   L_t = sum_{i + j = t} A_i V_j        (pairs with i + j > 8 are dropped:
-//                                         their weight is below 2^-56),
-// 28 BF16 products per output.  Digit i is stored pre-scaled as
-// d_i 2^{-8(i-3)} (exact in BF16: an integer of at most 8 significant bits
-// times a power of two), so that every pair of level t contributes
-// d_i d_j 2^{-8(t-6)}: one scale per level on both operands.
-//   * Levels 2..5 carry the leading bits and are summed exactly: the integer
-//     L_t over a K chunk of 128 is below 128 (2^16 + 2^15) < 2^24 (level 5, the
-//     largest), so the tensor core's FP32 accumulation of the scaled integers is
-//     exact; after every chunk the epilogue converts them (32-bit conversions),
-//     shifts them into place and adds them into one int64 per output, which
-//     stays exact over the whole K.
-//   * Levels 6..8 weigh at most 2^-32 of level 2; each has its own FP32
-//     accumulator over the whole K, read once at the end.  One shared
-//     accumulator for all three does not work: measured on GB300, adding the
-//     small levels into the larger running sum loses their low bits with a
-//     bias (the accumulation truncates), and the error grew linearly in K to
-//     ~1e-11 relative at K = 8192; with one accumulator per level it is 5e-15.
-// The result is A*V to within ~2^-53 K max|A_m.| max|V_.c| per entry, the
-// accuracy class of an FP64 GEMM.
+// Integer operands.  Every row m of the (stacked real) left operand is scaled by
+// 2^{57 - e_m} (max_k |L[m,k]| < 2^{e_m}) and every column c of the right
+// operand by 2^{57 - f_c}; each scaled entry is rounded to the nearest integer,
+// so |L_int|, |V_int| <= 2^57 and the rounding error is at most 2^-58 of the
+// row (column) scale.  The product of the integer matrices
+//   X[m, c] = sum_k L_int[m, k] V_int[k, c],   |X| <= K 2^114,
+// is computed EXACTLY, and (A V)[m, c] = 2^{e_m + f_c - 114} X[m, c] is then
+// within K 2^-57 max_k|L[m,k]| max_k|V[k,c]| of the exact product: the accuracy
+// class of an FP64 GEMM.
 //
-// Two kernels per product (oz_part_kernel), 320 threads each: a TMA producer warp,
-// an MMA warp that allocates TMEM and issues tcgen05.mma.kind::f16 (M 128, K 16)
-// from one thread, and 8 epilogue warps reading TMEM with tcgen05.ld.
-//   * tail (levels 6..8): 128 x 128 tiles, 3 accumulators x 128 TMEM columns,
-//     two 112 KB stages of all 7 A and 7 V digit tiles per 32-wide K block, 36
-//     MMAs per block; K may be split freely; writes 2^{e-48} sum_t acc_t per
-//     output (one FP64 slab per split).
-//   * exact (levels 2..5): 128 x 64 tiles, digit planes 1..4 only (no pair of
-//     these levels uses a higher digit), four 48 KB stages, 20 MMAs per block;
-//     two sets of the 4 level accumulators (2 x 4 x 64 columns) so that the
-//     epilogue converts one 128-wide K chunk (32-bit conversions, shifted into an
-//     int64 per output) while the next accumulates; adds the tail values and
-//     applies the Chebyshev three-term update (or writes split-K partials).
-// Measured on GB300 (probes with the digit-pair patterns fed from shared memory):
-// 48 cycles per M128 N64 K16 MMA for 7 interleaved accumulators, 32 per N64
-// equivalent at N = 128 with 3 accumulators; the split runs the 18 tail pairs at
-// the wider tile.
-// Digit slicing is integer arithmetic on the FP64 bit patterns (FP64 issues at
-// 2 per clock per SM on this part; the integer pipes at 64).
+// Exact integer product by the Chinese remainder theorem.  With S = 17 pairwise
+// coprime moduli p_j <= 256 (product P ~ 2^132.95 > 2 K 2^114 for K <= 2^17),
+// X is recovered from its residues X mod p_j.  Each residue needs one product
+// of residue matrices: L_int mod p_j and V_int mod p_j are stored in symmetric
+// range (|r| <= 128, exact in BF16), so one BF16 tensor-core product per
+// modulus forms sum_k (L mod p)(V mod p), whose partial sums over a K chunk of
+// 1024 stay within 1024 * 128^2 = 2^24 and are therefore exact in the tensor
+// core's FP32 accumulator; the epilogue adds the chunks as 32-bit integers and
+// reduces mod p_j at the end.  17 BF16 products replace the FP64 product.
+// Reconstruction (crt_kernel): X = sum_j r_j C_j mod P with C_j = (P/p_j) *
+// ((P/p_j)^{-1} mod p_j), in 160-bit integer arithmetic (32-bit limbs), mapped
+// to the symmetric range (-P/2, P/2] and rounded once to FP64.
+//
+// Modular product kernel (ozm_kernel): one CTA per (128-row block, column tile
+// of BN <= 256 columns, modulus[, K split]).  A TMA producer warp, one thread
+// issuing tcgen05.mma.cta_group::1.kind::f16 (M 128, N BN, K 16) into one of two
+// TMEM accumulators (2 x 256 columns: the epilogue reads one K chunk while the
+// next accumulates), and 16 epilogue warps that read TMEM with tcgen05.ld.
+// Operand stages: 64-wide K blocks with 128-byte swizzle, 4 stages of 48 KB.
+// Measured on GB300 (one tensor-core MMA per 64-wide block and operand pair):
+// the tensor core reads its operands from shared memory at ~128 B per clock,
+// which a 128 x N(<=256) tile with one accumulator keeps near the math rate,
+// while several narrow accumulators per tile (the first Ozaki scheme's digit
+// pairs) left it bound by shared-memory traffic.
 // All mbarrier waits are bounded; on expiry the kernel records the failure in
 // the device status word, waits (bounded) for its copies and MMAs in flight,
 // frees its TMEM and returns.
@@ -66,15 +54,101 @@ namespace chase {
 
 namespace {
 
-constexpr int OZ_S = 7;          // digits per entry
-constexpr int OZ_B = 8;          // bits per digit
-constexpr int OZ_T0 = 6;         // first tail level; digit i is stored as d_i 2^{-8(i - 3)}
-constexpr int OBM = 128, OBK = 32;
-constexpr int OZ_CHUNK_KB = 4;   // 4 K blocks = 128 K per exact chunk
-constexpr int OZ_EPI_WARPS = 8;
-constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
+// ---------------------------------------------------------------------------
+// Moduli and CRT constants (computed at compile time)
+// ---------------------------------------------------------------------------
+constexpr int OZ_KBITS = 57;  // integer operands: |x_int| <= 2^57
+// 17 pairwise coprime moduli <= 256 (256 = 2^8; 255 = 3 5 17; 253 = 11 23; 247 = 13 19;
+// 217 = 7 31; the others prime): P = prod p_j ~ 2^132.95 > 2 * 2^17 * 2^114.
+__host__ __device__ constexpr int oz_modulus(int j) {
+  constexpr int t[kOzModuli] = {256, 255, 253, 251, 247, 241, 239, 233, 229,
+                                227, 223, 217, 211, 199, 197, 193, 191};
+  return t[j];
+}
+static_assert(kOzPlaneBytes == 2 * kOzModuli, "workspace plane size");
+static_assert(kOzMaxK <= (1 << 17), "K bound of the modulus product");
+
+struct Big {  // unsigned 160-bit integer, little-endian 32-bit limbs
+  uint32_t w[5];
+};
+
+constexpr Big big_small(uint32_t x) { return Big{{x, 0, 0, 0, 0}}; }
+constexpr Big big_mul_small(Big a, uint32_t k) {
+  uint64_t c = 0;
+  for (int i = 0; i < 5; ++i) {
+    const uint64_t t = (uint64_t)a.w[i] * k + c;
+    a.w[i] = (uint32_t)t;
+    c = t >> 32;
+  }
+  return a;
+}
+constexpr uint32_t big_mod_small(Big a, uint32_t p) {
+  uint64_t r = 0;
+  for (int i = 4; i >= 0; --i) r = ((r << 32) | a.w[i]) % p;
+  return (uint32_t)r;
+}
+constexpr Big big_shr1(Big a) {
+  for (int i = 0; i < 5; ++i) a.w[i] = (a.w[i] >> 1) | (i < 4 ? (a.w[i + 1] << 31) : 0u);
+  return a;
+}
+constexpr uint32_t inv_mod(uint32_t a, uint32_t p) {  // a^{-1} mod p, gcd(a, p) = 1
+  long long t = 0, nt = 1, r = p, nr = a % p;
+  while (nr != 0) {
+    const long long q = r / nr;
+    long long tmp = t - q * nt; t = nt; nt = tmp;
+    tmp = r - q * nr; r = nr; nr = tmp;
+  }
+  return (uint32_t)(t < 0 ? t + p : t);
+}
+
+struct CrtTable {
+  int p[kOzModuli];          // the moduli
+  uint32_t C[kOzModuli][5];  // C_j = (P / p_j) ((P / p_j)^{-1} mod p_j) < P
+  uint32_t P[5];
+  uint32_t Ph[5];            // P / 2
+  double invP;               // 1 / P (rounded)
+};
+
+constexpr CrtTable make_crt_table() {
+  CrtTable t{};
+  Big P = big_small(1);
+  for (int j = 0; j < kOzModuli; ++j) {
+    t.p[j] = oz_modulus(j);
+    P = big_mul_small(P, (uint32_t)oz_modulus(j));
+  }
+  for (int j = 0; j < kOzModuli; ++j) {
+    Big Mj = big_small(1);
+    for (int i = 0; i < kOzModuli; ++i)
+      if (i != j) Mj = big_mul_small(Mj, (uint32_t)oz_modulus(i));
+    const uint32_t inv = inv_mod(big_mod_small(Mj, (uint32_t)oz_modulus(j)), (uint32_t)oz_modulus(j));
+    const Big Cj = big_mul_small(Mj, inv);
+    for (int l = 0; l < 5; ++l) t.C[j][l] = Cj.w[l];
+  }
+  const Big Ph = big_shr1(P);
+  double pd = 0.0;
+  for (int l = 4; l >= 0; --l) {
+    t.P[l] = P.w[l];
+    t.Ph[l] = Ph.w[l];
+    pd = pd * 4294967296.0 + (double)P.w[l];
+  }
+  t.invP = 1.0 / pd;
+  return t;
+}
+
+__constant__ CrtTable c_crt = make_crt_table();
+
+constexpr int MBM = 128, MBK = 64, MNST = 4;
+constexpr int MBN_MAX = 256;
+constexpr int M_EPI_WARPS = 16;
+constexpr int M_THREADS = 64 + 32 * M_EPI_WARPS;
+constexpr int M_CHUNK_KB = 16;  // 16 x 64 = 1024 K per exact chunk: |partial| <= 1024 * 2^14
+constexpr int M_A_T = MBM * MBK * 2;          // 16 KB
+constexpr int M_B_T = MBN_MAX * MBK * 2;      // 32 KB
+constexpr int M_STG = M_A_T + M_B_T;          // 48 KB
+constexpr int M_SMEM = MNST * M_STG + 1024 + 256;
+static_assert(M_SMEM <= 232448, "shared memory");
+static_assert(M_STG % 1024 == 0, "stage alignment (128-byte swizzle atoms)");
 constexpr long long kOzWait = 4000000000LL;
-static_assert(kOzPlaneBytes == 2 * OZ_S, "workspace plane size");
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -114,16 +188,23 @@ __device__ __forceinline__ void tma3(void* dst, const CUtensorMap* m, uint64_t* 
       "l"((uint64_t)m), "r"(s32(b)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
-// Shared-memory matrix descriptor, K-major, 64-byte swizzle: rows of 64 bytes (32 BF16
-// of K), 8-row groups 512 bytes apart.
-__device__ __forceinline__ uint64_t desc_sw64(uint32_t a) {
-  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: rows of 128 bytes (64 BF16
+// of K), 8-row groups 1024 bytes apart.  The K16 step k of a block starts 32 k bytes in.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t a) {
+  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 __device__ __forceinline__ void commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    s32(b))
                : "memory");
+}
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void ld32(uint32_t taddr, uint32_t* r) {
   asm volatile(
@@ -135,117 +216,41 @@ __device__ __forceinline__ void ld32(uint32_t taddr, uint32_t* r) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
-// Level-split product: the exact levels 2..5 and the tail levels 6..8 as two
-// kernels.  The tail kernel needs no per-chunk readout, so with three
-// accumulators it runs 128-wide N tiles (3 x 128 TMEM columns), which the tensor
-// core feeds ~1.5x faster per flop than 64-wide ones; it may split K freely and
-// writes its FP64 values (one slab per split) for the exact kernel.  The exact
-// kernel reads only digit planes 1..4 of each operand (no pair of levels 2..5 uses
-// a higher digit), keeps two sets of its four level accumulators (2 x 4 x 64 TMEM
-// columns) so that the epilogue reads one chunk while the next accumulates, and
-// adds the tail values before the three-term update.
+// Modular products: R[z][c][r] = (sum_{k in split} Lres_j[r, k] Vres_j[k, c]) mod p_j,
+// z = split * S + j (grid z).  Lres planes row-major (rows x kp), Vres planes column-major
+// (kp x ncols); both K-padded with zeros to kp (a multiple of 64).
 // ---------------------------------------------------------------------------
-template <bool kTail>
-struct PartCfg {
-  static constexpr int BN = kTail ? 128 : 64;
-  static constexpr int PLANES = kTail ? OZ_S : 4;          // digit planes read
-  static constexpr int NST = kTail ? 2 : 4;                // stages
-  static constexpr int A_T = OBM * OBK * 2;                // 8 KB
-  static constexpr int V_T = BN * OBK * 2;                 // 4 or 8 KB
-  static constexpr int STG = PLANES * (A_T + V_T);         // 48 or 112 KB
-  static constexpr int SMEM = NST * STG + 1024 + 256;
-  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
-                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(OBM >> 4) << 24);
-};
-static_assert(PartCfg<true>::SMEM <= 232448 && PartCfg<false>::SMEM <= 232448, "shared memory");
-static_assert(3 * PartCfg<true>::BN <= 512 && 2 * 4 * PartCfg<false>::BN <= 512, "TMEM");
-static_assert(PartCfg<true>::STG % 1024 == 0 && PartCfg<false>::STG % 1024 == 0, "stage alignment");
-
-__device__ __forceinline__ void mma_n(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                      uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-// MMAs of one K block of the part's levels.  Accumulator of level t: tail t - 6 at
-// column (t - 6) BN; exact t - 2 at column buf 4 BN + (t - 2) BN.  restart: the first
-// MMA into each accumulator (pair i = 1, K-step 0) overwrites it.
-template <bool kTail>
-__device__ __forceinline__ void issue_part(uint32_t tmem, uint32_t buf, uint64_t da0, uint64_t dv0,
-                                           bool restart) {
-  using C = PartCfg<kTail>;
-#pragma unroll
-  for (int t = kTail ? OZ_T0 : 2; t <= (kTail ? OZ_S + 1 : OZ_T0 - 1); ++t) {
-#pragma unroll
-    for (int i = 1; i <= OZ_S; ++i) {
-      const int j = t - i;
-      if (j < 1 || j > OZ_S) continue;
-      const uint32_t col = kTail ? (uint32_t)((t - OZ_T0) * C::BN)
-                                 : (uint32_t)(buf * 4 * C::BN + (t - 2) * C::BN);
-      const uint64_t da = da0 + (uint64_t)(((i - 1) * C::A_T) >> 4);
-      const uint64_t dv = dv0 + (uint64_t)(((j - 1) * C::V_T) >> 4);
-#pragma unroll
-      for (int kk = 0; kk < OBK / 16; ++kk) {
-        const uint64_t off = (uint64_t)((kk * 32) >> 4);
-        mma_n(tmem + col, da + off, dv + off, C::IDESC, (i == 1 && kk == 0 && restart) ? 0u : 1u);
-      }
-    }
-  }
-}
-
-// kTail: tail[z][r + c M] = 2^{e - 48} sum_{t >= 6} acc_t over this CTA's K range (z = split).
-// !kTail: v = 2^{e - 40} G1 (+ sum_z tail[z] when this is split 0), then partial[z] or the
-// three-term update into out64.
-template <bool kTail>
-__global__ void __launch_bounds__(OZ_THREADS, 1)
-    oz_part_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
-                   int M, int N, int nkb_total, int kbs, int col0, const int* __restrict__ rowexp,
-                   const int* __restrict__ colexp, double alpha, double beta, const double* X64,
-                   double gamma, const double* Z64, double* out64, int ldo,
-                   double* __restrict__ partial, double* tail, int tail_splits,
-                   DevStatus* status) {
-  using C = PartCfg<kTail>;
+__global__ void __launch_bounds__(M_THREADS, 1)
+    ozm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
+               int M, int N, int BN, int col0, int nkb_total, int kbs, uint8_t* __restrict__ R,
+               DevStatus* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + C::NST * C::STG);
-  uint64_t* full = bars;                 // [NST]
-  uint64_t* empty = bars + C::NST;       // [NST]
-  uint64_t* cfull = bars + 2 * C::NST;   // [2] exact chunk accumulated in buffer b
-  uint64_t* cfree = cfull + 2;           // [2] buffer b read out
-  uint64_t* tdone = cfree + 2;           // every MMA finished
+  uint64_t* bars = (uint64_t*)(smem + MNST * M_STG);
+  uint64_t* full = bars;                // [MNST]
+  uint64_t* empty = bars + MNST;        // [MNST]
+  uint64_t* cfull = bars + 2 * MNST;    // [2] chunk accumulated in buffer b
+  uint64_t* cfree = cfull + 2;          // [2] buffer b read out
+  uint64_t* tdone = cfree + 2;          // every MMA finished
   uint32_t* tslot = (uint32_t*)(tdone + 1);
   int* s_err = (int*)(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * C::BN, m0 = blockIdx.y * OBM;
-  const int kbeg = blockIdx.z * kbs;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * MBM;
+  const int jm = blockIdx.z % kOzModuli, split = blockIdx.z / kOzModuli;
+  const int kbeg = split * kbs;
   const int nkb = max(0, min(kbs, nkb_total - kbeg));
-  const int nchunks = (nkb + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
+  const int nchunks = (nkb + M_CHUNK_KB - 1) / M_CHUNK_KB;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < C::NST; ++i) { bar_init(&full[i], 1); bar_init(&empty[i], 1); }
-    for (int b = 0; b < 2; ++b) { bar_init(&cfull[b], 1); bar_init(&cfree[b], OZ_EPI_WARPS); }
+    for (int i = 0; i < MNST; ++i) { bar_init(&full[i], 1); bar_init(&empty[i], 1); }
+    for (int b = 0; b < 2; ++b) { bar_init(&cfull[b], 1); bar_init(&cfree[b], M_EPI_WARPS); }
     bar_init(tdone, 1);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(tslot)),
@@ -259,134 +264,101 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- producer ----------------
+    const uint32_t bytes = (uint32_t)(M_A_T + BN * MBK * 2);
     int issued = 0;
     for (int kb = 0; kb < nkb && !*(volatile int*)s_err; ++kb) {
-      const int s = kb % C::NST;
-      if (!bar_wait(&empty[s], (uint32_t)(((kb / C::NST) & 1) ^ 1))) { atomicOr(s_err, 1); break; }
-      bar_expect(&full[s], C::STG);
-      unsigned char* st = smem + s * C::STG;
-      const int x = (kbeg + kb) * OBK;
-      for (int i = 0; i < C::PLANES; ++i) tma3(st + i * C::A_T, &mapA, &full[s], x, m0, i);
-      for (int j = 0; j < C::PLANES; ++j)
-        tma3(st + C::PLANES * C::A_T + j * C::V_T, &mapV, &full[s], x, col0 + n0, j);
+      const int s = kb % MNST;
+      if (!bar_wait(&empty[s], (uint32_t)(((kb / MNST) & 1) ^ 1))) { atomicOr(s_err, 1); break; }
+      bar_expect(&full[s], bytes);
+      unsigned char* st = smem + s * M_STG;
+      const int x = (kbeg + kb) * MBK;
+      tma3(st, &mapA, &full[s], x, m0, jm);
+      tma3(st + M_A_T, &mapV, &full[s], x, col0 + n0, jm);
       issued = kb + 1;
     }
-    for (int b = max(0, issued - C::NST); b < issued; ++b)
-      if (!bar_wait(&full[b % C::NST], (uint32_t)((b / C::NST) & 1))) atomicOr(s_err, 1);
+    for (int b = max(0, issued - MNST); b < issued; ++b)
+      if (!bar_wait(&full[b % MNST], (uint32_t)((b / MNST) & 1))) atomicOr(s_err, 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(MBM >> 4) << 24);
     bool bad = false;
     for (int kb = 0; kb < nkb && !bad; ++kb) {
-      const int chunk = kb / OZ_CHUNK_KB;
-      const bool chunk_start = (kb % OZ_CHUNK_KB) == 0;
-      const bool chunk_last = (kb % OZ_CHUNK_KB) == OZ_CHUNK_KB - 1 || kb == nkb - 1;
+      const int chunk = kb / M_CHUNK_KB;
+      const bool cstart = (kb % M_CHUNK_KB) == 0;
+      const bool clast = (kb % M_CHUNK_KB) == M_CHUNK_KB - 1 || kb == nkb - 1;
       const uint32_t buf = (uint32_t)(chunk & 1);
-      if (!kTail && chunk_start && chunk >= 2) {
+      if (cstart && chunk >= 2) {
         // the epilogue has read this buffer's previous chunk (chunk - 2)
         if (!bar_wait(&cfree[buf], (uint32_t)(((chunk - 2) >> 1) & 1))) { bad = true; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
-      const int s = kb % C::NST;
-      if (!bar_wait(&full[s], (uint32_t)((kb / C::NST) & 1))) { bad = true; break; }
+      const int s = kb % MNST;
+      if (!bar_wait(&full[s], (uint32_t)((kb / MNST) & 1))) { bad = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = s32(smem + s * C::STG);
-      const uint64_t da0 = desc_sw64(sa), dv0 = desc_sw64(sa + C::PLANES * C::A_T);
-      issue_part<kTail>(tmem, buf, da0, dv0, kTail ? (kb == 0) : chunk_start);
-      if (!kTail && chunk_last) commit(&cfull[buf]);
+      const uint32_t sa = s32(smem + s * M_STG);
+      const uint64_t da = desc_sw128(sa), dv = desc_sw128(sa + M_A_T);
+#pragma unroll
+      for (int kk = 0; kk < MBK / 16; ++kk)
+        mma_f16(tmem + buf * MBN_MAX, da + (uint64_t)(kk * 2), dv + (uint64_t)(kk * 2), idesc,
+                (cstart && kk == 0) ? 0u : 1u);
       commit(&empty[s]);
+      if (clast) commit(&cfull[buf]);
     }
     if (bad) atomicOr(s_err, 2);
     commit(tdone);
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int q = warp & 3;
-    const int cg = (warp - 2) >> 2;  // column half of the tile
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 (the hardware's lane quarter of the warp)
+    // and the column quarter (w - 2) / 4 of the tile (BN / 4 <= 64 columns).
+    const int q = warp & 3, cq = (warp - 2) >> 2;
     const int r = m0 + 32 * q + lane;
-    const int er = (r < M) ? rowexp[r] : 0;
+    const int cw = BN >> 2;
+    int sum[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) sum[j] = 0;
     bool ok = true;
-    if constexpr (kTail) {
-      if (nkb > 0 && !__all_sync(0xffffffffu, bar_wait(tdone, 0u))) {
+    for (int c = 0; c < nchunks; ++c) {
+      const uint32_t buf = (uint32_t)(c & 1);
+      if (!__all_sync(0xffffffffu, bar_wait(&cfull[buf], (uint32_t)((c >> 1) & 1)))) {
         ok = false;
         if (lane == 0) atomicOr(s_err, 4);
+        break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (__shfl_sync(0xffffffffu, (int)(ok && !*(volatile int*)s_err), 0)) {
-        double* tz = tail + (size_t)blockIdx.z * M * N;
-#pragma unroll 1
-        for (int h = 0; h < C::BN / 2 / 16; ++h) {  // 4 groups of 16 columns of this half
-          const int cbase = cg * (C::BN / 2) + 16 * h;
-          double y[16];
+      const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + buf * MBN_MAX + (uint32_t)(cq * cw);
+      uint32_t v[32];
+      ld32(ta, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 16; ++j) y[j] = 0.0;
-          if (nkb > 0) {
-#pragma unroll 1
-            for (int t = OZ_S + 1; t >= OZ_T0; --t) {
-              uint32_t tl[16];
-              ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((t - OZ_T0) * C::BN + cbase), tl);
-#pragma unroll
-              for (int j = 0; j < 16; ++j) y[j] += (double)__uint_as_float(tl[j]);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int c = n0 + cbase + j;
-            if (r < M && c < N) {
-              const int e = er + colexp[col0 + c];
-              tz[(size_t)r + (size_t)c * M] = ldexp(y[j], e - OZ_B * 6);  // 2^{e-40} 2^-8 sum
-            }
-          }
-        }
+      for (int j = 0; j < 32; ++j) sum[j] += __float2int_rn(__uint_as_float(v[j]));
+      if (cw > 32) {
+        ld32(ta + 32, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       }
-    } else {
-      long long g1[32];
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0 && c + 2 < nchunks) bar_arrive(&cfree[buf]);
+      if (cw > 32) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) g1[j] = 0;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        const uint32_t buf = (uint32_t)(c & 1);
-        if (!__all_sync(0xffffffffu, bar_wait(&cfull[buf], (uint32_t)((c >> 1) & 1)))) {
-          ok = false;
-          if (lane == 0) atomicOr(s_err, 4);
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + buf * 4 * C::BN + (uint32_t)(cg * 32);
-#pragma unroll 1
-        for (int t = 2; t < OZ_T0; ++t) {
-          uint32_t rr[32];
-          ld32(tb + (uint32_t)((t - 2) * C::BN), rr);
-          const float unscale = __int_as_float((127 - OZ_B * (OZ_T0 - t)) << 23);
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            g1[j] += (long long)__float2int_rz(__uint_as_float(rr[j]) * unscale) << (OZ_B * (OZ_T0 - 1 - t));
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0 && c + 2 < nchunks) bar_arrive(&cfree[buf]);
+        for (int j = 0; j < 32; ++j) sum[32 + j] += __float2int_rn(__uint_as_float(v[j]));
       }
-      if (ok && nkb > 0 && !__all_sync(0xffffffffu, bar_wait(tdone, 0u))) {
-        ok = false;
-        if (lane == 0) atomicOr(s_err, 4);
-      }
-      if (nkb == 0) ok = true;
-      if (__shfl_sync(0xffffffffu, (int)(ok && !*(volatile int*)s_err), 0) && r < M) {
+    }
+    if (__shfl_sync(0xffffffffu, (int)(ok && !*(volatile int*)s_err), 0) && r < M) {
+      // sum mod p in [0, p): the float quotient of |sum| < 2^29 is off by at most one
+      const int pm = c_crt.p[jm];
+      const float ip = 1.0f / (float)pm;
+      uint8_t* Rz = R + (size_t)blockIdx.z * N * M;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int c = n0 + cg * 32 + j;
-          if (c < N) {
-            const int e = er + colexp[col0 + c];
-            double v0 = (nkb == 0) ? 0.0 : ldexp((double)g1[j], e - OZ_B * 5);
-            if (blockIdx.z == 0)
-              for (int z = 0; z < tail_splits; ++z) v0 += tail[(size_t)z * M * N + (size_t)r + (size_t)c * M];
-            if (partial) {
-              partial[(size_t)blockIdx.z * M * N + (size_t)r + (size_t)c * M] = v0;
-            } else {
-              const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
-              double v = alpha * v0;
-              if (beta != 0.0) v = fma(beta, X64[idx], v);
-              if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
-              out64[idx] = v;
-            }
-          }
+      for (int j = 0; j < 64; ++j) {
+        const int col = n0 + cq * cw + j;
+        if (j < cw && col - n0 < BN && col < N) {
+          const int sv = sum[j];
+          const int qq = (int)floorf((float)sv * ip);
+          int rr = sv - qq * pm;
+          if (rr < 0) rr += pm;
+          if (rr >= pm) rr -= pm;
+          Rz[(size_t)col * M + r] = (uint8_t)rr;
         }
       }
     }
@@ -394,32 +366,139 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
-    if (nkb > 0 && !bar_wait(tdone, 0u) && lane == 0) atomicOr(s_err, 8);
+    if (!bar_wait(tdone, 0u) && lane == 0) atomicOr(s_err, 8);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
   if (threadIdx.x == 32 && *s_err) atomicOr(&status->timeout, *s_err);
 }
 
-// Sum of the split-K partial results in a fixed order, then the three-term epilogue.
-__global__ void oz_reduce_kernel(int M, int N, int S, const double* __restrict__ P, int col0,
-                                 double alpha, double beta, const double* X64, double gamma,
-                                 const double* Z64, double* out64, int ldo) {
+// ---------------------------------------------------------------------------
+// CRT reconstruction and epilogue:
+//   v = 2^{e_r + f_c - 114} X,  X = CRT(residues) in (-P/2, P/2],
+//   out64[r + (col0 + c) ldo] = alpha v + beta X64[.] + gamma Z64[.]  (same index).
+// R holds `splits` partial residues per modulus; they are summed mod p_j first.
+// ---------------------------------------------------------------------------
+// Returns the FP64 rounding m of |X| and the sign, with X = m 2^{*shift}.
+__device__ __forceinline__ double crt_value(const uint8_t* __restrict__ R, size_t stride_z,
+                                            size_t idx, int splits, int* shift_out) {
+  unsigned long long acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+  for (int j = 0; j < kOzModuli; ++j) {
+    uint32_t rj = R[(size_t)j * stride_z + idx];
+    for (int s = 1; s < splits; ++s) rj += R[(size_t)(s * kOzModuli + j) * stride_z + idx];
+    rj %= (uint32_t)oz_modulus(j);
+#pragma unroll
+    for (int l = 0; l < 5; ++l) acc[l] += (unsigned long long)rj * c_crt.C[j][l];
+  }
+  uint32_t x[5];
+  unsigned long long carry = 0;
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    const unsigned long long t = acc[l] + carry;
+    x[l] = (uint32_t)t;
+    carry = t >> 32;
+  }
+  // X < 17 * 256 * P < 2^146: reduce mod P with q = floor(X / P) from the top limbs
+  const double xd = ((double)x[4] * 4294967296.0 + (double)x[3]) * 4294967296.0 + (double)x[2];
+  const unsigned int qv = (unsigned int)floor(xd * 18446744073709551616.0 * c_crt.invP);
+  {
+    unsigned long long borrow = 0, cq = 0;
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+      const unsigned long long prod = (unsigned long long)c_crt.P[l] * qv + cq;
+      cq = prod >> 32;
+      const unsigned long long sub = (unsigned long long)(uint32_t)prod + borrow;
+      const long long d = (long long)x[l] - (long long)sub;
+      x[l] = (uint32_t)d;
+      borrow = d < 0 ? 1ull : 0ull;
+    }
+    if (borrow) {  // q was one too large: add P back
+      unsigned long long c = 0;
+#pragma unroll
+      for (int l = 0; l < 5; ++l) {
+        const unsigned long long t = (unsigned long long)x[l] + c_crt.P[l] + c;
+        x[l] = (uint32_t)t;
+        c = t >> 32;
+      }
+    }
+  }
+  auto cmp_ge = [&](const uint32_t* b) {
+    for (int l = 4; l >= 0; --l) {
+      if (x[l] != b[l]) return x[l] > b[l];
+    }
+    return true;
+  };
+  if (cmp_ge(c_crt.P)) {  // q was one too small
+    long long br = 0;
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+      const long long d = (long long)x[l] - (long long)c_crt.P[l] - br;
+      x[l] = (uint32_t)d;
+      br = d < 0 ? 1 : 0;
+    }
+  }
+  // symmetric range: X > P/2 stands for X - P
+  bool neg = false;
+  bool gt_half = false;
+  for (int l = 4; l >= 0; --l) {
+    if (x[l] != c_crt.Ph[l]) { gt_half = x[l] > c_crt.Ph[l]; break; }
+  }
+  if (gt_half) {
+    neg = true;
+    long long br = 0;
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+      const long long d = (long long)c_crt.P[l] - (long long)x[l] - br;
+      x[l] = (uint32_t)d;
+      br = d < 0 ? 1 : 0;
+    }
+  }
+  // round the 160-bit magnitude once to FP64: the leading 64 bits (normalised) and a
+  // sticky bit for everything below them
+  int top = 4;
+  while (top > 0 && x[top] == 0) --top;
+  *shift_out = 0;
+  if (x[top] == 0) return 0.0;
+  const int lz = __clz(x[top]);
+  const uint32_t x1 = top >= 1 ? x[top - 1] : 0u, x2 = top >= 2 ? x[top - 2] : 0u;
+  unsigned long long hi = ((unsigned long long)x[top] << 32) | x1;
+  uint32_t rest = x2;
+  if (lz > 0) {
+    hi = (hi << lz) | (x2 >> (32 - lz));
+    rest = x2 << lz;
+  }
+  bool sticky = rest != 0;
+  for (int l = top - 3; l >= 0; --l) sticky |= x[l] != 0;
+  if (sticky) hi |= 1ull;
+  const double mag = __ull2double_rn(hi);
+  *shift_out = 32 * (top - 1) - lz;  // |X| = hi 2^shift
+  return neg ? -mag : mag;
+}
+
+__global__ void __launch_bounds__(256) crt_kernel(int M, int N, int splits, const uint8_t* __restrict__ R,
+                                                  const int* __restrict__ rowexp,
+                                                  const int* __restrict__ colexp, int col0,
+                                                  double alpha, double beta, const double* X64,
+                                                  double gamma, const double* Z64, double* out64,
+                                                  int ldo) {
   const size_t total = (size_t)M * N;
+  const size_t stride_z = total;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(t % M), c = (int)(t / M);
-    double y = 0.0;
-    for (int z = 0; z < S; ++z) y += P[(size_t)z * total + t];
+    int sh;
+    const double x = crt_value(R, stride_z, t, splits, &sh);
+    const double v0 = ldexp(x, sh + rowexp[r] + colexp[col0 + c] - 2 * OZ_KBITS);
     const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
-    double v = alpha * y;
+    double v = alpha * v0;
     if (beta != 0.0) v = fma(beta, X64[idx], v);
     if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
     out64[idx] = v;
   }
 }
 
-// ---------------- slicing ----------------
+// ---------------- residues of the integer operands ----------------
 
 // |x| as its IEEE bit pattern: for non-negative doubles the integer order is the numeric
 // order, so row / column maxima need no FP64 instructions (FP64 issues at 2 per clock per
@@ -436,42 +515,34 @@ __device__ __forceinline__ int exp_bound(unsigned long long amax_bits) {
   return e;
 }
 
-// Digits by rounding to nearest: d_1 in [-256, 256], d_i in [-128, 128] for i > 1 (the
-// remainder after a nearest rounding is at most half a unit), stored as d_i 2^{-8(i-3)},
-// all exact in BF16.  The slicing error is at most 2^-57 of the row / column scale and
-// unbiased, so it accumulates like a random walk over K instead of growing linearly as
-// truncation's one-signed error does.
-// Integer form: R = round(x 2^{56 - e}) (|R| < 2^56, from the significand and exponent
-// fields), then balanced base-256 digits from the top, d = floor((R + 2^{s-1}) / 2^s),
-// R -= d 2^s for s = 48, 40, ..., 8, and the last digit the remainder.
-__device__ __forceinline__ void write_digits(double x, int e, __nv_bfloat16* base, size_t idx,
-                                             size_t plane) {
+// x_int = round(x 2^{57 - e}) (|x| < 2^e, so |x_int| <= 2^57), from the significand and
+// exponent fields; then its residues mod p_j in symmetric range, stored as BF16 (exact:
+// integers of magnitude <= 128) in plane j.
+__device__ __forceinline__ void write_residues(double x, int e, __nv_bfloat16* base, size_t idx,
+                                               size_t plane) {
   const long long bits = __double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   long long m = bits & ((1LL << 52) - 1);
-  long long R = 0;
+  long long X = 0;
   if (ex != 0x7FF) {
     int sh;
     if (ex == 0) {
-      sh = 1 - 1075 + 56 - e;  // subnormal: x = m 2^-1074
+      sh = 1 - 1075 + OZ_KBITS - e;  // subnormal: x = m 2^-1074
     } else {
       m |= 1LL << 52;
-      sh = ex - 1075 + 56 - e;  // x = m 2^{ex - 1075}; |x| < 2^e gives m 2^sh < 2^56
+      sh = ex - 1075 + OZ_KBITS - e;  // x = m 2^{ex - 1075}; |x| < 2^e gives m 2^sh < 2^57
     }
-    if (sh >= 0) R = m << sh;
-    else if (sh > -64) R = (m + (1LL << (-sh - 1))) >> (-sh);
-    if (bits < 0) R = -R;
+    if (sh >= 0) X = m << sh;
+    else if (sh > -64) X = (m + (1LL << (-sh - 1))) >> (-sh);
+    if (bits < 0) X = -X;
   }
 #pragma unroll
-  for (int i = 0; i < OZ_S; ++i) {
-    const int s = OZ_B * (OZ_S - 1 - i);
-    long long d = R;
-    if (s > 0) {
-      d = (R + (1LL << (s - 1))) >> s;
-      R -= d << s;
-    }
-    const float v = __int2float_rn((int)d) * __int_as_float((127 + OZ_B * (2 - i)) << 23);
-    base[idx + (size_t)i * plane] = __float2bfloat16_rz(v);  // exact: 8 significant bits
+  for (int j = 0; j < kOzModuli; ++j) {
+    const int p = oz_modulus(j);
+    int rr = (int)(X % p);  // in (-p, p), sign of X
+    if (rr > p / 2) rr -= p;
+    else if (rr < -(p / 2)) rr += p;
+    base[idx + (size_t)j * plane] = __int2bfloat16_rn(rr);  // exact: |rr| <= 128
   }
 }
 
@@ -484,22 +555,22 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long v, un
   __syncthreads();
   if (lane == 0) red[wi] = v;
   __syncthreads();
-  unsigned long long m = 0;
-  for (int i = 0; i < nw; ++i) m = red[i] > m ? red[i] : m;
-  return m;
+  unsigned long long mx = 0;
+  for (int i = 0; i < nw; ++i) mx = red[i] > mx ? red[i] : mx;
+  return mx;
 }
 
-// Stacked real A (M = n or 2n): digits of row m into planes (row-major, ld kp), row
+// Stacked real A (M = n or 2n): residues of row m into planes (row-major, ld kp), row
 // exponent into rowexp[m].  Row m of Ahat = column m of Ahat (symmetric), read from A.
 template <class T>
 __global__ void __launch_bounds__(256) oz_slice_A_kernel(int n, const T* __restrict__ A, int lda,
                                                          int kp, __nv_bfloat16* planes,
                                                          size_t plane, int* rowexp) {
   __shared__ unsigned long long red[8];
-  const int M = Sc<T>::cplx ? 2 * n : n;
   const int m = blockIdx.x;
   const int mm = m % n;
   const bool mre = m < n;
+  const int M = Sc<T>::cplx ? 2 * n : n;
   auto elem = [&](int k) -> double {
     if constexpr (Sc<T>::cplx) {
       const z64 a = A[(size_t)(k % n) + (size_t)mm * lda];  // A[k mod n, mm]
@@ -518,11 +589,11 @@ __global__ void __launch_bounds__(256) oz_slice_A_kernel(int n, const T* __restr
   if (threadIdx.x == 0) rowexp[m] = e;
   for (int k = threadIdx.x; k < kp; k += 256) {
     const double x = (k < M) ? elem(k) : 0.0;
-    write_digits(x, e, planes, (size_t)m * kp + k, plane);
+    write_residues(x, e, planes, (size_t)m * kp + k, plane);
   }
 }
 
-// FP64 stacked block V64 (M x ncols, ld ldi): digits of column c into planes
+// FP64 stacked block V64 (M x ncols, ld ldi): residues of column c into planes
 // (column-major, ld kp; rows >= M zero), column exponent into colexp[c].
 __global__ void __launch_bounds__(256) oz_slice_V_kernel(int M, int c0, const double* __restrict__ V64,
                                                          int ldi, int kp, __nv_bfloat16* planes,
@@ -539,7 +610,7 @@ __global__ void __launch_bounds__(256) oz_slice_V_kernel(int M, int c0, const do
   if (threadIdx.x == 0) colexp[c] = e;
   for (int k = threadIdx.x; k < kp; k += 256) {
     const double x = (k < M) ? col[k] : 0.0;
-    write_digits(x, e, planes, (size_t)c * kp + k, plane);
+    write_residues(x, e, planes, (size_t)c * kp + k, plane);
   }
 }
 
@@ -564,8 +635,8 @@ __global__ void stack_V_kernel(int n, int ncols, const T* __restrict__ V, int ld
 }
 
 // Xt (l x n, ld ldt) is the transpose of a column-major X (n x l): row m of X is column m
-// of Xt.  Digits of the rows of the stacked operator [[Xr, -Xi], [Xi, Xr]] (2n x 2l; real:
-// X itself, n x l) into planes (row-major, ld kp), row exponents into rowexp.
+// of Xt.  Residues of the rows of the stacked operator [[Xr, -Xi], [Xi, Xr]] (2n x 2l;
+// real: X itself, n x l) into planes (row-major, ld kp), row exponents into rowexp.
 template <class T>
 __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, int l, const T* __restrict__ Xt,
                                                             int ldt, int kp, __nv_bfloat16* planes,
@@ -595,11 +666,11 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, int l, const 
   if (threadIdx.x == 0) rowexp[m] = e;
   for (int k = threadIdx.x; k < kp; k += 256) {
     const double x = (k < K) ? elem(k) : 0.0;
-    write_digits(x, e, planes, (size_t)m * kp + k, plane);
+    write_residues(x, e, planes, (size_t)m * kp + k, plane);
   }
 }
 
-// Digits of the columns of a block Y (n x q, ld ldy) in stacked form: plane column j < q
+// Residues of the columns of a block Y (n x q, ld ldy) in stacked form: plane column j < q
 // holds [Re Y; Im Y][:, j]; with `pair` (complex only) plane column q + j holds the stacked
 // -i Y[:, j] = [Im Y; -Re Y][:, j].  Then, with X's columns as the left operand's rows,
 // Xhat^T [Yhat | stack(-i Y)] = [Re(X^H Y) | Im(X^H Y)].  Both columns of a pair share the
@@ -640,8 +711,8 @@ __global__ void __launch_bounds__(512) oz_slice_cols_kernel(int n, int q, const 
         x = col[k];
       }
     }
-    write_digits(x, e, planes, (size_t)j * kp + k, plane);
-    if (pair) write_digits(y, e, planes, (size_t)(q + j) * kp + k, plane);
+    write_residues(x, e, planes, (size_t)j * kp + k, plane);
+    if (pair) write_residues(y, e, planes, (size_t)(q + j) * kp + k, plane);
   }
 }
 
@@ -688,24 +759,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-// 3-D BF16 map over S digit planes: {kp (contiguous), rows, S}, box {32, box_rows, 1};
-// consecutive planes are plane_rows * kp elements apart (plane_rows >= rows).
+// 3-D BF16 map over the residue planes: {kp (contiguous), rows, S}, box {64, box_rows, 1},
+// 128-byte swizzle; consecutive planes are plane_rows * kp elements apart.
 int make_map3(CUtensorMap* map, const void* base, int kp, int rows, int plane_rows, int box_rows) {
   auto enc = encoder();
   if (!enc) return CHASE_ERR_CUDA;
-  cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)OZ_S};
+  cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)kOzModuli};
   cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * 2 * (cuuint64_t)plane_rows};
-  cuuint32_t box[3] = {OBK, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {MBK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : CHASE_ERR_CUDA;
 }
 
 }  // namespace
 
-size_t oz_plane_elems(int rows, int kp) { return (size_t)rows * kp; }
+size_t oz_residue_bytes(int M, int N) {
+  return (size_t)kOzMaxSplits * kOzModuli * (size_t)M * (size_t)N;
+}
 
 template <class T>
 int oz_slice_A(cudaStream_t st, int n, const T* A, int lda, int kp, void* planes, int* rowexp,
@@ -729,58 +802,40 @@ int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ld
 }
 
 int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
-            int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
-            double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
-            DevStatus* dst, Scratch scr, Scratch tailbuf, int* launches) {
-  if (N <= 0) return 0;
-  CUtensorMap mA, mV64, mV128;
+            int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0,
+            int N, double alpha, double beta, const double* X64, double gamma, const double* Z64,
+            double* out64, int ldo, DevStatus* dst, Scratch resbuf, int* launches) {
+  if (N <= 0 || M <= 0) return 0;
+  if (kp % MBK != 0 || kp > kOzMaxK) return CHASE_ERR_UNSUPPORTED;
   if (a_plane_rows < M) a_plane_rows = M;
-  if (make_map3(&mA, Aplanes, kp, M, a_plane_rows, OBM) ||
-      make_map3(&mV64, Vplanes, kp, ncols_total, ncols_total, PartCfg<false>::BN) ||
-      make_map3(&mV128, Vplanes, kp, ncols_total, ncols_total, PartCfg<true>::BN))
+  // column tiles of at most 256 (a multiple of 16), as even as possible
+  const int ntile = ceil_div(N, MBN_MAX);
+  const int BN = ceil_div(ceil_div(N, ntile), 16) * 16;
+  CUtensorMap mA, mV;
+  if (make_map3(&mA, Aplanes, kp, M, a_plane_rows, MBM) ||
+      make_map3(&mV, Vplanes, kp, ncols_total, ncols_total, BN))
     return CHASE_ERR_CUDA;
-  CHASE_CUDA_TRY(cudaFuncSetAttribute(oz_part_kernel<true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      PartCfg<true>::SMEM));
-  CHASE_CUDA_TRY(cudaFuncSetAttribute(oz_part_kernel<false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      PartCfg<false>::SMEM));
-  const int nkb = kp / OBK;
-  const size_t slab = (size_t)M * N * sizeof(double);
-  if (slab > tailbuf.bytes) return CHASE_ERR_OOM;
-  // tail levels: split K freely (no exact chunks) up to about four waves of CTAs, one
-  // slab of FP64 values per split
-  const int tiles_t = ceil_div(N, PartCfg<true>::BN) * ceil_div(M, OBM);
-  int St = std::max(1, std::min(nkb, ceil_div(4 * kNumSMs, tiles_t)));
-  while (St > 1 && (size_t)St * slab > tailbuf.bytes) --St;
-  const int kbs_t = ceil_div(nkb, St);
-  St = ceil_div(nkb, kbs_t);
-  double* tail = (double*)tailbuf.ptr;
-  dim3 grid_t(ceil_div(N, PartCfg<true>::BN), ceil_div(M, OBM), St);
-  oz_part_kernel<true><<<grid_t, OZ_THREADS, PartCfg<true>::SMEM, st>>>(
-      mA, mV128, M, N, nkb, kbs_t, col0, rowexp, colexp, 0.0, 0.0, nullptr, 0.0, nullptr, nullptr, 0,
-      nullptr, tail, 0, dst);
-  if (launches) ++*launches;
-  // exact levels: split K in whole chunks until there are about four waves of CTAs
-  const int tiles = ceil_div(N, PartCfg<false>::BN) * ceil_div(M, OBM);
-  const int nchunks = ceil_div(nkb, OZ_CHUNK_KB);
-  int S = std::max(1, std::min(nchunks, ceil_div(4 * kNumSMs, tiles)));
-  while (S > 1 && (size_t)S * slab > scr.bytes) --S;
-  const int kbs = ceil_div(nchunks, S) * OZ_CHUNK_KB;
+  CHASE_CUDA_TRY(cudaFuncSetAttribute(ozm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM));
+  const int nkb = kp / MBK;
+  const int mblk = ceil_div(M, MBM);
+  const size_t slab = (size_t)kOzModuli * (size_t)M * N;  // residue bytes of one split
+  // split K (whole 1024-wide chunks) until there are about four waves of CTAs
+  const int nchunks = ceil_div(nkb, M_CHUNK_KB);
+  int S = std::max(1, std::min(nchunks, ceil_div(4 * kNumSMs, ntile * mblk * kOzModuli)));
+  S = std::min(S, kOzMaxSplits);
+  while (S > 1 && (size_t)S * slab > resbuf.bytes) --S;
+  if (slab > resbuf.bytes) return CHASE_ERR_OOM;
+  const int kbs = ceil_div(nchunks, S) * M_CHUNK_KB;
   S = ceil_div(nkb, kbs);
-  double* partial = (S > 1) ? (double*)scr.ptr : nullptr;
-  dim3 grid(ceil_div(N, PartCfg<false>::BN), ceil_div(M, OBM), S);
-  oz_part_kernel<false><<<grid, OZ_THREADS, PartCfg<false>::SMEM, st>>>(
-      mA, mV64, M, N, nkb, kbs, col0, rowexp, colexp, alpha, beta, X64, gamma, Z64, out64, ldo,
-      partial, tail, St, dst);
+  uint8_t* R = (uint8_t*)resbuf.ptr;
+  dim3 grid(ntile, mblk, kOzModuli * S);
+  ozm_kernel<<<grid, M_THREADS, M_SMEM, st>>>(mA, mV, M, N, BN, col0, nkb, kbs, R, dst);
   if (launches) ++*launches;
-  if (S > 1) {
-    const size_t total = (size_t)M * N;
-    const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16);
-    oz_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, S, partial, col0, alpha, beta, X64, gamma, Z64,
-                                             out64, ldo);
-    if (launches) ++*launches;
-  }
+  const size_t total = (size_t)M * N;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16));
+  crt_kernel<<<blocks, 256, 0, st>>>(M, N, S, R, rowexp, colexp, col0, alpha, beta, X64, gamma, Z64,
+                                     out64, ldo);
+  if (launches) ++*launches;
   CHASE_CUDA_TRY(cudaGetLastError());
   return 0;
 }

@@ -90,10 +90,16 @@ int tc_filter_step(cudaStream_t st, int M, int kp, const void* Ah, const void* A
                    double* out64, int ldv, void* Vh_out, void* Vl_out, DevStatus* dst,
                    int* launches);
 
-// ---- FP64-accurate Ozaki-scheme products on BF16 tensor cores (gemm_oz.cu) -
-// 7 BF16 digit planes per operand.  A planes: row-major (M x kp), V planes:
-// column-major (kp x ncols_total).
-constexpr size_t kOzPlaneBytes = 14;  // bytes of digit planes per operand element
+// ---- FP64-accurate products on BF16 tensor cores (gemm_oz.cu, Ozaki scheme II) -
+// Operands become 57-bit integers (one power-of-two scale per row / column); their
+// residues mod 17 pairwise coprime moduli <= 256 are BF16 planes.  A planes: row-major
+// (M x kp), V planes: column-major (kp x ncols); kp = K rounded up to 64 (zero padded).
+constexpr int kOzModuli = 17;                   // residue planes per operand
+constexpr size_t kOzPlaneBytes = 2 * kOzModuli; // bytes of residue planes per operand element
+constexpr int kOzMaxSplits = 2;                 // K splits of one product (residue slabs)
+constexpr int kOzMaxK = 1 << 17;                // longest K the moduli's product covers
+// Device bytes of the residue buffer oz_gemm needs for an M x N product.
+size_t oz_residue_bytes(int M, int N);
 template <class T>
 int oz_slice_A(cudaStream_t st, int n, const T* A, int lda, int kp, void* planes, int* rowexp,
                int* launches);
@@ -102,11 +108,11 @@ int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ld
 template <class T>
 int oz_stack_V(cudaStream_t st, int n, int ncols, const T* V, int ldv, double* V64, int ldo,
                int* launches);
-// Row digits of the stacked operator of a general X given as Xt = X^T (l x n, ld ldt).
+// Row residues of the stacked operator of a general X given as Xt = X^T (l x n, ld ldt).
 template <class T>
 int oz_slice_rows(cudaStream_t st, int n, int l, const T* Xt, int ldt, int kp, void* planes,
                   int* rowexp, int* launches);
-// Column digits of a block Y (n x q): plane column j = stacked Y[:, j] and, with pair
+// Column residues of a block Y (n x q): plane column j = stacked Y[:, j] and, with pair
 // (complex only), plane column q + j = stacked (-i Y[:, j]); plane stride (q or 2q) * kp.
 template <class T>
 int oz_slice_cols(cudaStream_t st, int n, int q, const T* Y, int ldy, int kp, bool pair,
@@ -117,13 +123,13 @@ int oz_gram_assemble(cudaStream_t st, int l, const double* out, int ldo, T* G, i
 template <class T>
 int transpose(cudaStream_t st, int n, int l, const T* X, int ldx, T* Xt, int ldt, int* launches);
 // out64[:, col0 + c] = alpha * (A V)[:, col0 + c] + beta * X64 + gamma * Z64 for c < N.
-// A's planes are a_plane_rows * kp elements apart (0: M * kp).  scr: split-K partials of
-// the exact levels; tailbuf: FP64 values of the tail levels, at least M * N doubles (more
-// lets the tail kernel split K).
+// A's planes are a_plane_rows * kp elements apart (0: M * kp).  resbuf: residues of the
+// modular products, at least oz_residue_bytes(M, N) / kOzMaxSplits bytes (twice that lets
+// the product split K).  kp must be a multiple of 64 and at most kOzMaxK.
 int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
             int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
-            DevStatus* dst, Scratch scr, Scratch tailbuf, int* launches);
+            DevStatus* dst, Scratch resbuf, int* launches);
 
 // ---- failure path of the bounded device waits (selftest.cu) ----------------
 // One thread waits (at most `seconds`) on an mbarrier nothing arrives on and sets

@@ -318,7 +318,7 @@ struct OzBufs {
   void* Vp = nullptr;
   int* colexp = nullptr;
   double* V64[2] = {nullptr, nullptr};
-  Scratch tail{nullptr, 0};  // FP64 values of the tail levels (two M x ncols slabs)
+  Scratch res{nullptr, 0};  // residues of the modular products (oz_residue_bytes(kp, ncols))
 };
 
 template <class T>
@@ -326,7 +326,7 @@ size_t oz_bytes(int n, int ncols) {
   const int M = Sc<T>::cplx ? 2 * n : n;
   const size_t kp = (size_t)tc_kpad(M);
   return align256(kOzPlaneBytes * (size_t)M * kp) + align256(4 * (size_t)M) + align256(kOzPlaneBytes * kp * ncols) +
-         align256(4 * (size_t)ncols) + 2 * align256(8 * kp * ncols) + align256(16 * kp * ncols);
+         align256(4 * (size_t)ncols) + 2 * align256(8 * kp * ncols) + align256(oz_residue_bytes((int)kp, ncols));
 }
 
 template <class T>
@@ -341,8 +341,8 @@ OzBufs oz_carve(char* base, int n, int ncols) {
   B.Vp = base + off; off += align256(kOzPlaneBytes * (size_t)B.kp * ncols);
   B.colexp = (int*)(base + off); off += align256(4 * (size_t)ncols);
   for (int i = 0; i < 2; ++i) { B.V64[i] = (double*)(base + off); off += align256(8 * (size_t)B.kp * ncols); }
-  B.tail = Scratch{base + off, 16 * (size_t)B.kp * ncols};
-  off += align256(16 * (size_t)B.kp * ncols);
+  B.res = Scratch{base + off, oz_residue_bytes(B.kp, ncols)};
+  off += align256(oz_residue_bytes(B.kp, ncols));
   return B;
 }
 
@@ -381,7 +381,7 @@ int filter_oz_enqueue(chase_ctx* h, int n, const T* A, int lda, bool split_A, in
     TRY(oz_slice_V(st, M, first, ncols, B.V64[in], kp, kp, ncols, B.Vp, B.colexp, &h->launches));
     h->product_timer.begin(st);
     TRY(oz_gemm(st, M, kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, ncols, first, act, alpha, beta,
-                B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, scr, B.tail, &h->launches));
+                B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, B.res, &h->launches));
     h->product_timer.end(st);
     if (flops) *flops += per_col * act;
     if (steps) ++*steps;
@@ -467,7 +467,7 @@ int aq_oz(chase_ctx* h, int n, const T* Q, int nu, T* AQ, OzBufs& B, Scratch scr
   TRY(oz_stack_V<T>(st, n, nu, Q, n, B.V64[0], B.kp, &h->launches));
   TRY(oz_slice_V(st, B.M, 0, nu, B.V64[0], B.kp, B.kp, B.ncols, B.Vp, B.colexp, &h->launches));
   TRY(oz_gemm(st, B.M, B.kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, B.ncols, 0, nu, 1.0, 0.0, nullptr,
-              0.0, nullptr, B.V64[1], B.kp, h->dstat, scr, B.tail, &h->launches));
+              0.0, nullptr, B.V64[1], B.kp, h->dstat, B.res, &h->launches));
   TRY(tc_unstack_V<T>(st, n, 0, nu, B.V64[1], B.kp, AQ, n, &h->launches));
   return 0;
 }
@@ -488,7 +488,7 @@ struct OzProd {
   double* B64 = nullptr;                      // kpl x l stacked small factor
   double* out = nullptr;                      // FP64 result staging, max(M, 2l) x l
   void* Xt = nullptr;                         // X^T (l x n)
-  Scratch tail{nullptr, 0};                   // tail-level values, two staging sizes
+  Scratch res{nullptr, 0};                    // residues of the modular products
 };
 
 template <class T>
@@ -501,7 +501,7 @@ size_t ozp_bytes(int n, int l) {
          align256(kOzPlaneBytes * (size_t)M * kpl) + align256(4 * (size_t)M) + align256(kOzPlaneBytes * kpl * l) +
          align256(4 * (size_t)l) + align256(8 * kpl * l) +
          align256(8 * std::max<size_t>(M, wl) * l) + align256(sizeof(T) * (size_t)n * l) +
-         align256(16 * std::max<size_t>(M, wl) * l);
+         align256(oz_residue_bytes((int)std::max<size_t>(M, wl), l));
 }
 
 template <class T>
@@ -525,7 +525,8 @@ OzProd ozp_carve(char* base, int n, int l) {
   P.B64 = (double*)take(8 * (size_t)P.kpl * l);
   P.out = (double*)take(8 * std::max<size_t>(P.M, wl) * l);
   P.Xt = take(sizeof(T) * (size_t)n * l);
-  P.tail = Scratch{take(16 * std::max<size_t>(P.M, wl) * l), 16 * std::max<size_t>(P.M, wl) * l};
+  const size_t rb = oz_residue_bytes((int)std::max<size_t>(P.M, wl), l);
+  P.res = Scratch{take(rb), rb};
   return P;
 }
 
@@ -548,7 +549,7 @@ int oz_gram(chase_ctx* h, OzProd& P, int q, const T* X, int ldx, const T* Y, int
     plane_rows = q;
   }
   TRY(oz_gemm(st, q, P.kp, left, lexp, plane_rows, P.Gp, P.gexp, wq, 0, wq, 1.0, 0.0, nullptr, 0.0,
-              nullptr, P.out, q, h->dstat, scr, P.tail, &h->launches));
+              nullptr, P.out, q, h->dstat, P.res, &h->launches));
   TRY(oz_gram_assemble<T>(st, q, P.out, q, G, ldg, &h->launches));
   return 0;
 }
@@ -573,7 +574,7 @@ int oz_tall(chase_ctx* h, OzProd& P, int kl, const T* X, int ldx, int N, T* Y, i
   TRY(transpose<T>(st, P.n, kl, X, ldx, Xt, kl, &h->launches));
   TRY(oz_slice_rows<T>(st, P.n, kl, Xt, kl, P.kpl, P.Rp, P.rexp, &h->launches));
   TRY(oz_gemm(st, P.M, P.kpl, P.Rp, P.rexp, 0, P.Bp, P.bexp, N, 0, N, 1.0, 0.0, nullptr, 0.0,
-              nullptr, P.out, P.M, h->dstat, scr, P.tail, &h->launches));
+              nullptr, P.out, P.M, h->dstat, P.res, &h->launches));
   TRY(tc_unstack_V<T>(st, P.n, 0, N, P.out, P.M, Y, ldy, &h->launches));
   return 0;
 }
