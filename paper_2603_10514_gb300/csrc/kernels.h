@@ -45,6 +45,10 @@ int householder_qr(cudaStream_t st, int n, int l, T* X, int ldx, T* Vh, int ldv,
 // ---- parallel cyclic Jacobi eigensolver (jacobi.cu) ------------------------
 // Diagonalises the Hermitian H (l x l, overwritten).  Eigenvalues (ascending)
 // go to dw (device) and eigenvectors to W.  Returns sweeps used through *sweeps.
+// One cooperative launch runs every sweep; work: jacobi_work_bytes(l, sizeof(T)) bytes.
+// Returns 5 (CHASE_ERR_TIMEOUT) if a bounded grid-barrier wait ran out.
+constexpr int kJacobiMaxCtas = 1216;  // 8 CTAs of 256 threads on each of the 152 SMs
+size_t jacobi_work_bytes(int l, size_t elem);
 template <class T>
 int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw, void* work,
                size_t work_bytes, int max_sweeps, int* sweeps, int* launches);

@@ -218,7 +218,7 @@ size_t lanczos_work_bytes(size_t elem, int n, int nruns, int m) {
   const size_t ps = (size_t)n * nruns;
   return al(elem * ps * (m + 1)) + al(elem * ps) + al(elem * (size_t)nruns * (m + 1)) +
          2 * al(8 * (size_t)nruns * m) + 2 * al(8 * (size_t)m * m) + al(8 * (size_t)m) +
-         /* jacobi */ 3 * al(8 * (size_t)m * m) + al(64 * (size_t)(m + 2)) + 4096;
+         /* jacobi */ al(jacobi_work_bytes(m, sizeof(double))) + 256;
 }
 
 template int lanczos_bounds<double>(cudaStream_t, int, const double*, int, int, const double*, int,

@@ -143,7 +143,7 @@ Layout layout_for(int n, int l) {
   L.Ri = off; off += sq;
   L.H = off; off += sq;
   L.Wm = off; off += sq;
-  L.jac = off; off += 2 * sq + align256(64 * (size_t)(l + 2)) + 1536;
+  L.jac = off; off += align256(jacobi_work_bytes(l, sizeof(T)));
   L.dw = off; off += align256(sizeof(double) * (size_t)l);
   L.dres = off; off += align256(sizeof(double) * (size_t)l);
   L.scratch = off; off += kScratchBytes;
