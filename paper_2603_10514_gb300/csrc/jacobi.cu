@@ -33,11 +33,12 @@ namespace chase {
 
 namespace {
 
-struct Rot {
+struct __align__(16) Rot {
   int p, q;
   double c;
   double sx, sy;  // s e^{i phi}
 };
+static_assert(sizeof(Rot) == 32, "two 16-byte loads");
 
 __device__ inline void pair_of(int L, int round, int i, int& p, int& q) {
   // circle of L-1 players (0..L-2) rotating around a fixed player L-1
@@ -59,93 +60,127 @@ template <> __device__ inline z64 ldcg<z64>(const z64* p) {
   return z64{v.x, v.y};
 }
 
-// Rotation i of round `round` from the current H.
+template <class T> __device__ inline T rot_s(const Rot& r);
+template <> __device__ inline double rot_s<double>(const Rot& r) { return r.sx; }
+template <> __device__ inline z64 rot_s<z64>(const Rot& r) { return z64{r.sx, r.sy}; }
+
+// Rotation annihilating g = H_pq from the entries H_pp, H_qq, H_pq of the current H.
 template <class T>
-__device__ inline Rot make_rot(int l, int L, int round, int i, const T* H, int ldh) {
-  int p, q;
-  pair_of(L, round, i, p, q);
+__device__ inline Rot rot_from(int p, int q, double hpp, double hqq, T g) {
   Rot r;
   r.p = p; r.q = q; r.c = 1.0; r.sx = 0.0; r.sy = 0.0;
-  if (q < l) {
-    T g = ldcg(H + (size_t)p + (size_t)q * ldh);
-    double ag = sqrt(Sc<T>::abs2(g));
-    if (ag > 0.0) {
-      double hpp = Sc<T>::re(ldcg(H + (size_t)p + (size_t)p * ldh));
-      double hqq = Sc<T>::re(ldcg(H + (size_t)q + (size_t)q * ldh));
-      double tau = (hqq - hpp) / (2.0 * ag);
-      double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-      double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-      r.c = c;
-      if constexpr (Sc<T>::cplx) {
-        r.sx = s * g.x / ag;
-        r.sy = s * g.y / ag;
-      } else {
-        r.sx = s * (g > 0.0 ? 1.0 : -1.0);
-        r.sy = 0.0;
-      }
+  double ag = sqrt(Sc<T>::abs2(g));
+  if (ag > 0.0) {
+    double tau = (hqq - hpp) / (2.0 * ag);
+    double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+    r.c = c;
+    if constexpr (Sc<T>::cplx) {
+      r.sx = s * g.x / ag;
+      r.sy = s * g.y / ag;
+    } else {
+      r.sx = s * (g > 0.0 ? 1.0 : -1.0);
+      r.sy = 0.0;
     }
   }
   return r;
 }
 
-template <class T> __device__ inline T rot_s(const Rot& r);
-template <> __device__ inline double rot_s<double>(const Rot& r) { return r.sx; }
-template <> __device__ inline z64 rot_s<z64>(const Rot& r) { return z64{r.sx, r.sy}; }
-
-__device__ inline Rot load_rot(const Rot* r) {
+__device__ inline Rot load_rot(const Rot* r) {  // two 16-byte loads through L2
+  const int4 a = __ldcg((const int4*)r);
+  const double2 b = __ldcg((const double2*)r + 1);
   Rot o;
-  o.p = __ldcg(&r->p); o.q = __ldcg(&r->q);
-  o.c = __ldcg(&r->c); o.sx = __ldcg(&r->sx); o.sy = __ldcg(&r->sy);
+  o.p = a.x;
+  o.q = a.y;
+  o.c = __hiloint2double(a.w, a.z);
+  o.sx = b.x;
+  o.sy = b.y;
   return o;
 }
 
-// Work item t of a round's update: t < np^2 is the 2x2 block (pair a rows, pair b columns)
-// of H <- J^H H J (a <= b; block (b, a) is written as its conjugate transpose), the
-// others (row i, pair b) of W <- W J.
+// The 2x2 block (rows of pair a, columns of pair b) of J^H H J: loads the block of the
+// current H (Hc, ld ldc; a dummy index gives a zero row / column) and returns
+// o = {o_pp, o_qp, o_pq, o_qq}.  Used by the owner of the block and, for three entries,
+// by the threads that form the next round's rotations: the same arithmetic, so the same
+// values.
 template <class T>
-__device__ inline void apply_item(long long t, int l, int np, const Rot* __restrict__ rots, T* H,
-                                  int ldh, T* W, int ldw) {
+__device__ inline void block_update(int l, const Rot& ra, const Rot& rb, const T* Hc, int ldc, T* o) {
+  const int pa = ra.p, qa = ra.q, pb = rb.p, qb = rb.q;
+  const bool va = qa < l, vb = qb < l;
+  T h_pp = ldcg(Hc + (size_t)pa + (size_t)pb * ldc);
+  T h_qp = va ? ldcg(Hc + (size_t)qa + (size_t)pb * ldc) : Sc<T>::zero();
+  T h_pq = vb ? ldcg(Hc + (size_t)pa + (size_t)qb * ldc) : Sc<T>::zero();
+  T h_qq = (va && vb) ? ldcg(Hc + (size_t)qa + (size_t)qb * ldc) : Sc<T>::zero();
+  // right: [col p, col q] J_b = [c col_p - conj(s) col_q, s col_p + c col_q]
+  const double cb = rb.c;
+  const T sb = rot_s<T>(rb), sbc = Sc<T>::conj(sb);
+  T r_pp = Sc<T>::sub(Sc<T>::scale(h_pp, cb), Sc<T>::mul(h_pq, sbc));
+  T r_qp = Sc<T>::sub(Sc<T>::scale(h_qp, cb), Sc<T>::mul(h_qq, sbc));
+  T r_pq = Sc<T>::add(Sc<T>::mul(h_pp, sb), Sc<T>::scale(h_pq, cb));
+  T r_qq = Sc<T>::add(Sc<T>::mul(h_qp, sb), Sc<T>::scale(h_qq, cb));
+  // left: J_a^H [row p; row q] = [c row_p - s row_q; conj(s) row_p + c row_q]
+  const double ca = ra.c;
+  const T sa = rot_s<T>(ra), sac = Sc<T>::conj(sa);
+  o[0] = Sc<T>::sub(Sc<T>::scale(r_pp, ca), Sc<T>::mul(sa, r_qp));
+  o[2] = Sc<T>::sub(Sc<T>::scale(r_pq, ca), Sc<T>::mul(sa, r_qq));
+  o[1] = Sc<T>::add(Sc<T>::mul(sac, r_pp), Sc<T>::scale(r_qp, ca));
+  o[3] = Sc<T>::add(Sc<T>::mul(sac, r_pq), Sc<T>::scale(r_qq, ca));
+  if (ra.p == rb.p) {  // the rotated pair itself: exact zero off-diagonal, real diagonal
+    o[2] = Sc<T>::zero();
+    o[1] = Sc<T>::zero();
+    o[0] = Sc<T>::from_re(Sc<T>::re(o[0]));
+    o[3] = Sc<T>::from_re(Sc<T>::re(o[3]));
+  }
+}
+
+// Index of the pair that holds x in round `round` (inverse of pair_of).
+__device__ inline int pair_index(int L, int round, int x) {
+  const int m = L - 1;
+  if (x == m || x == round % m) return 0;
+  const int d = ((x - round) % m + m) % m;  // 1 .. m - 1
+  return d <= (m - 1) / 2 ? d : m - d;
+}
+
+// Entry (x, y) of the next H (x != y or x == y), formed from the current H and the
+// round's rotations exactly as the owner of its block forms it.
+template <class T>
+__device__ inline T next_entry(int l, int L, int round, const Rot* rots, const T* Hc, int ldc, int x,
+                               int y) {
+  const int ax = pair_index(L, round, x), ay = pair_index(L, round, y);
+  const int a = ax < ay ? ax : ay, b = ax < ay ? ay : ax;
+  const Rot ra = load_rot(rots + a), rb = load_rot(rots + b);
+  T o[4];
+  block_update<T>(l, ra, rb, Hc, ldc, o);
+  // block (a, b) holds rows {ra.p, ra.q} x columns {rb.p, rb.q}; (x, y) or its mirror
+  const int r = ax <= ay ? x : y, c = ax <= ay ? y : x;
+  const T v = (r == ra.p) ? (c == rb.p ? o[0] : o[2]) : (c == rb.p ? o[1] : o[3]);
+  return ax <= ay ? v : Sc<T>::conj(v);
+}
+
+// Work item t of a round's update, from the current H (Hc) into the next (Hn): t < np^2
+// is the 2x2 block (pair a rows, pair b columns) of J^H H J (a <= b; block (b, a) is
+// written as its conjugate transpose); the others (row i, pair b) of W <- W J in place.
+template <class T>
+__device__ inline void apply_item(long long t, int l, int np, const Rot* __restrict__ rots,
+                                  const T* Hc, int ldc, T* Hn, int ldn, T* W, int ldw) {
   const long long nblk = (long long)np * np;
   if (t < nblk) {
     const int a = (int)(t % np), b = (int)(t / np);
     if (a > b) return;  // written by block (b, a) as its conjugate transpose
     const Rot ra = load_rot(rots + a), rb = load_rot(rots + b);
+    T o[4];
+    block_update<T>(l, ra, rb, Hc, ldc, o);
     const int pa = ra.p, qa = ra.q, pb = rb.p, qb = rb.q;
     const bool va = qa < l, vb = qb < l;
-    // load the 2x2 block (dummy index -> zero row/column, never stored)
-    T h_pp = ldcg(H + (size_t)pa + (size_t)pb * ldh);
-    T h_qp = va ? ldcg(H + (size_t)qa + (size_t)pb * ldh) : Sc<T>::zero();
-    T h_pq = vb ? ldcg(H + (size_t)pa + (size_t)qb * ldh) : Sc<T>::zero();
-    T h_qq = (va && vb) ? ldcg(H + (size_t)qa + (size_t)qb * ldh) : Sc<T>::zero();
-    // right: [col p, col q] J_b = [c col_p - conj(s) col_q, s col_p + c col_q]
-    const double cb = rb.c;
-    const T sb = rot_s<T>(rb), sbc = Sc<T>::conj(sb);
-    T r_pp = Sc<T>::sub(Sc<T>::scale(h_pp, cb), Sc<T>::mul(h_pq, sbc));
-    T r_qp = Sc<T>::sub(Sc<T>::scale(h_qp, cb), Sc<T>::mul(h_qq, sbc));
-    T r_pq = Sc<T>::add(Sc<T>::mul(h_pp, sb), Sc<T>::scale(h_pq, cb));
-    T r_qq = Sc<T>::add(Sc<T>::mul(h_qp, sb), Sc<T>::scale(h_qq, cb));
-    // left: J_a^H [row p; row q] = [c row_p - s row_q; conj(s) row_p + c row_q]
-    const double ca = ra.c;
-    const T sa = rot_s<T>(ra), sac = Sc<T>::conj(sa);
-    T o_pp = Sc<T>::sub(Sc<T>::scale(r_pp, ca), Sc<T>::mul(sa, r_qp));
-    T o_pq = Sc<T>::sub(Sc<T>::scale(r_pq, ca), Sc<T>::mul(sa, r_qq));
-    T o_qp = Sc<T>::add(Sc<T>::mul(sac, r_pp), Sc<T>::scale(r_qp, ca));
-    T o_qq = Sc<T>::add(Sc<T>::mul(sac, r_pq), Sc<T>::scale(r_qq, ca));
-    if (a == b) {  // the rotated pair itself: exact zero off-diagonal, real diagonal
-      o_pq = Sc<T>::zero();
-      o_qp = Sc<T>::zero();
-      o_pp = Sc<T>::from_re(Sc<T>::re(o_pp));
-      o_qq = Sc<T>::from_re(Sc<T>::re(o_qq));
-    }
-    H[(size_t)pa + (size_t)pb * ldh] = o_pp;
-    if (va) H[(size_t)qa + (size_t)pb * ldh] = o_qp;
-    if (vb) H[(size_t)pa + (size_t)qb * ldh] = o_pq;
-    if (va && vb) H[(size_t)qa + (size_t)qb * ldh] = o_qq;
+    Hn[(size_t)pa + (size_t)pb * ldn] = o[0];
+    if (va) Hn[(size_t)qa + (size_t)pb * ldn] = o[1];
+    if (vb) Hn[(size_t)pa + (size_t)qb * ldn] = o[2];
+    if (va && vb) Hn[(size_t)qa + (size_t)qb * ldn] = o[3];
     if (a != b) {  // mirror: rows of pair b, columns of pair a
-      H[(size_t)pb + (size_t)pa * ldh] = Sc<T>::conj(o_pp);
-      if (va) H[(size_t)pb + (size_t)qa * ldh] = Sc<T>::conj(o_qp);
-      if (vb) H[(size_t)qb + (size_t)pa * ldh] = Sc<T>::conj(o_pq);
-      if (va && vb) H[(size_t)qb + (size_t)qa * ldh] = Sc<T>::conj(o_qq);
+      Hn[(size_t)pb + (size_t)pa * ldn] = Sc<T>::conj(o[0]);
+      if (va) Hn[(size_t)pb + (size_t)qa * ldn] = Sc<T>::conj(o[1]);
+      if (vb) Hn[(size_t)qb + (size_t)pa * ldn] = Sc<T>::conj(o[2]);
+      if (va && vb) Hn[(size_t)qb + (size_t)qa * ldn] = Sc<T>::conj(o[3]);
     }
   } else {
     const long long u = t - nblk;
@@ -162,40 +197,35 @@ __device__ inline void apply_item(long long t, int l, int np, const Rot* __restr
   }
 }
 
-// Grid-wide barrier of a cooperative launch, bounded: returns false (and the caller leaves
-// the kernel) when the wait ran out or another CTA gave up.
+// Grid-wide barrier of a cooperative launch on a counter that only grows: barrier k ends
+// once all G CTAs have added their arrival (count >= (k + 1) G).  One release-add per CTA
+// and acquire polls with a short back-off.  Bounded: returns false (the caller leaves the
+// kernel) when the wait ran out or another CTA gave up.
 struct GridBar {
   unsigned count;
-  unsigned gen;
   int abort;
   int sweeps;
+  int pad;
 };
 constexpr long long kBarWait = 2000000000LL;  // ~1 s of clock64
 
-__device__ bool grid_barrier(GridBar* gb, unsigned nblocks) {
+__device__ bool grid_barrier(GridBar* gb, unsigned nblocks, unsigned& k) {
   __shared__ int s_ok;
   __syncthreads();
   if (nblocks == 1) return true;  // one CTA: the block barrier orders its global writes
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &gb->gen;
-    volatile int* vab = &gb->abort;
     int ok = 1;
-    const unsigned g = *vgen;
-    __threadfence();
-    if (*vab) {
-      ok = 0;
-    } else if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == g) {
-        if (*vab) { ok = 0; break; }
-        if (clock64() - t0 > kBarWait) { atomicExch(&gb->abort, 1); ok = 0; break; }
-      }
+    const unsigned target = (++k) * nblocks;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->count) : "memory");
+    const long long t0 = clock64();
+    while (true) {
+      unsigned c;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(&gb->count) : "memory");
+      if ((int)(c - target) >= 0) break;
+      if (*(volatile int*)&gb->abort) { ok = 0; break; }
+      if (clock64() - t0 > kBarWait) { atomicExch(&gb->abort, 1); ok = 0; break; }
+      __nanosleep(20);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -203,11 +233,15 @@ __device__ bool grid_barrier(GridBar* gb, unsigned nblocks) {
 }
 
 // The whole cyclic Jacobi iteration: sweeps until ||off(H)||_F <= l u ||H||_F or
-// max_sweeps.  partial: 2 doubles per CTA.  gb->sweeps receives the sweep count.
+// max_sweeps.  H alternates between H0 (ld ld0) and H1 (ld ld1) every round (the next
+// round's rotations are formed from the previous H while the round writes the next one,
+// so a round needs one grid barrier); after an odd number of rounds the result is in H1.
+// rots: two sets of L/2 rotations; partial: 2 doubles per CTA; gb->sweeps: sweeps done.
 template <class T>
-__global__ void __launch_bounds__(256) jacobi_sweeps_kernel(int l, int L, T* H, int ldh, T* W,
-                                                            int ldw, Rot* rots, double* partial,
-                                                            GridBar* gb, int max_sweeps) {
+__global__ void __launch_bounds__(256) jacobi_sweeps_kernel(int l, int L, T* H0, int ld0, T* H1,
+                                                            int ld1, T* W, int ldw, Rot* rots,
+                                                            double* partial, GridBar* gb,
+                                                            int max_sweeps) {
   const unsigned G = gridDim.x;
   const int np = L / 2;
   const long long items = (long long)np * np + (long long)l * np;
@@ -215,15 +249,19 @@ __global__ void __launch_bounds__(256) jacobi_sweeps_kernel(int l, int L, T* H, 
   const long long gstride = (long long)G * blockDim.x;
   __shared__ double r0[8], r1[8];
   const double tolr = 1.1102230246251565e-16 * (double)l;
+  unsigned k = 0;   // barriers passed
+  int cur = 0;      // buffer holding the current H
   int sw = 0;
   for (; sw <= max_sweeps; ++sw) {
+    T* Hc = cur ? H1 : H0;
+    const int ldc = cur ? ld1 : ld0;
     // ||off(H)||_F^2 and ||H||_F^2: partial sums per CTA, then the same fixed-order total
     // in every CTA
     double off = 0.0, all = 0.0;
     const size_t total = (size_t)l * l;
     for (size_t t = gtid; t < total; t += (size_t)gstride) {
       const int i = (int)(t % l), j = (int)(t / l);
-      const double a = Sc<T>::abs2(ldcg(H + (size_t)i + (size_t)j * ldh));
+      const double a = Sc<T>::abs2(ldcg(Hc + (size_t)i + (size_t)j * ldc));
       all += a;
       if (i != j) off += a;
     }
@@ -240,22 +278,53 @@ __global__ void __launch_bounds__(256) jacobi_sweeps_kernel(int l, int L, T* H, 
       partial[2 * blockIdx.x] = a;
       partial[2 * blockIdx.x + 1] = b;
     }
-    if (!grid_barrier(gb, G)) return;
+    // rotations of the sweep's first round, from the current H
+    for (int i = blockIdx.x + G * threadIdx.x; i < np; i += G * blockDim.x) {
+      int p, q;
+      pair_of(L, 0, i, p, q);
+      Rot rr;
+      rr.p = p; rr.q = q; rr.c = 1.0; rr.sx = 0.0; rr.sy = 0.0;
+      if (q < l)
+        rr = rot_from<T>(p, q, Sc<T>::re(ldcg(Hc + (size_t)p + (size_t)p * ldc)),
+                         Sc<T>::re(ldcg(Hc + (size_t)q + (size_t)q * ldc)),
+                         ldcg(Hc + (size_t)p + (size_t)q * ldc));
+      rots[i] = rr;
+    }
+    if (!grid_barrier(gb, G, k)) return;
     double so = 0.0, sa = 0.0;
     for (unsigned b = 0; b < G; ++b) { so += __ldcg(partial + 2 * b); sa += __ldcg(partial + 2 * b + 1); }
     if (so <= tolr * tolr * sa || so == 0.0 || sw == max_sweeps) break;
     for (int r = 0; r < L - 1; ++r) {
-      // rotations, spread over the CTAs (their FP64 square roots and divisions)
-      for (int i = blockIdx.x + G * threadIdx.x; i < np; i += G * blockDim.x)
-        rots[i] = make_rot<T>(l, L, r, i, H, ldh);
-      if (!grid_barrier(gb, G)) return;
-      for (long long t = gtid; t < items; t += gstride) apply_item<T>(t, l, np, rots, H, ldh, W, ldw);
-      if (!grid_barrier(gb, G)) return;
+      const T* Hcr = cur ? H1 : H0;
+      T* Hn = cur ? H0 : H1;
+      const int ldcr = cur ? ld1 : ld0, ldn = cur ? ld0 : ld1;
+      const Rot* rc = rots + (size_t)(r & 1) * np;
+      Rot* rn = rots + (size_t)((r + 1) & 1) * np;
+      // the next round's rotations (spread over the CTAs: their FP64 square roots and
+      // divisions), from the entries this round writes, formed here from the current H
+      if (r + 1 < L - 1) {
+        for (int i = blockIdx.x + G * threadIdx.x; i < np; i += G * blockDim.x) {
+          int p, q;
+          pair_of(L, r + 1, i, p, q);
+          Rot rr;
+          rr.p = p; rr.q = q; rr.c = 1.0; rr.sx = 0.0; rr.sy = 0.0;
+          if (q < l)
+            rr = rot_from<T>(p, q, Sc<T>::re(next_entry<T>(l, L, r, rc, Hcr, ldcr, p, p)),
+                             Sc<T>::re(next_entry<T>(l, L, r, rc, Hcr, ldcr, q, q)),
+                             next_entry<T>(l, L, r, rc, Hcr, ldcr, p, q));
+          rn[i] = rr;
+        }
+      }
+      for (long long t = gtid; t < items; t += gstride)
+        apply_item<T>(t, l, np, rc, Hcr, ldcr, Hn, ldn, W, ldw);
+      cur ^= 1;
+      if (!grid_barrier(gb, G, k)) return;
     }
-    // the partial sums of the next check are written after two more barriers: no CTA
-    // still reads this sweep's values by then
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) gb->sweeps = sw;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    gb->sweeps = sw;
+    gb->pad = cur;
+  }
 }
 
 template <class T>
@@ -302,21 +371,22 @@ __global__ void permute_cols_kernel(int l, const T* W, int ldw, const int* perm,
 size_t jacobi_work_bytes(int l, size_t elem) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int L = (l % 2) ? l + 1 : l;
-  return al(sizeof(Rot) * (size_t)(L / 2 + 1)) + al(sizeof(GridBar)) + al(16 * (size_t)kJacobiMaxCtas) +
+  return al(sizeof(Rot) * (size_t)L) + al(sizeof(GridBar)) + al(16 * (size_t)kJacobiMaxCtas) +
          al(sizeof(int) * (size_t)l) + al(elem * (size_t)l * l);
 }
 
 template <class T>
 int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw, void* work,
-               size_t work_bytes, int max_sweeps, int* sweeps, int* launches) {
+               size_t work_bytes, int max_sweeps, int* sweeps, int* launches, int ctas) {
   if (l <= 0) return 0;
   const int L = (l % 2) ? l + 1 : l;
   if (jacobi_work_bytes(l, sizeof(T)) > work_bytes) return 4;  // CHASE_ERR_OOM
-  // workspace: rotations | barrier | per-CTA norm partials | permutation | W copy
+  // workspace: two sets of rotations | barrier | per-CTA norm partials | permutation |
+  // l x l buffer (the second H of the sweeps, then a copy of W)
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   char* base = (char*)work;
   Rot* rots = (Rot*)base;
-  base += al(sizeof(Rot) * (size_t)(L / 2 + 1));
+  base += al(sizeof(Rot) * (size_t)L);
   GridBar* gb = (GridBar*)base;
   base += al(sizeof(GridBar));
   double* partial = (double*)base;
@@ -329,8 +399,11 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
   jacobi_init_kernel<T><<<blocks, 256, 0, st>>>(l, W, ldw);
   ++nl;
   int sw = 0;
+  const T* Hfin = H;
+  int ldfin = ldh;
   if (l > 1) {
-    // CTAs: about 4 work items of a round per thread, at most one wave of co-resident CTAs
+    // CTAs: about 2 work items of a round per thread (measured: fewer CTAs leave the FP64
+    // work latency-bound, more make the grid barrier dearer), at most one co-resident wave
     static int max_coresident[2] = {0, 0};
     int& mc = max_coresident[Sc<T>::cplx ? 1 : 0];
     if (mc == 0) {
@@ -339,11 +412,13 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
       mc = std::max(1, std::min(per_sm * kNumSMs, kJacobiMaxCtas));
     }
     const long long items = (long long)(L / 2) * (L / 2) + (long long)l * (L / 2);
-    const int G = std::max(1, std::min(mc, ceil_div(items, 256 * 4)));
+    int G = std::max(1, std::min(mc, ceil_div(items, 256 * 2)));
+    if (ctas > 0) G = std::min(mc, ctas);
     CHASE_CUDA_TRY(cudaMemsetAsync(gb, 0, sizeof(GridBar), st));
-    int ms = max_sweeps;
-    void* args[] = {(void*)&l, (void*)&L, (void*)&H, (void*)&ldh, (void*)&W, (void*)&ldw, (void*)&rots,
-                    (void*)&partial, (void*)&gb, (void*)&ms};
+    int ms = max_sweeps, ld1 = l;
+    T* H1 = Wtmp;
+    void* args[] = {(void*)&l,   (void*)&L,   (void*)&H,    (void*)&ldh,     (void*)&H1, (void*)&ld1,
+                    (void*)&W,   (void*)&ldw, (void*)&rots, (void*)&partial, (void*)&gb, (void*)&ms};
     CHASE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_sweeps_kernel<T>, dim3(G), dim3(256),
                                                args, 0, st));
     ++nl;
@@ -355,8 +430,12 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
       return 5;  // CHASE_ERR_TIMEOUT
     }
     sw = hb.sweeps;
+    if (hb.pad) {  // the last round wrote the second buffer
+      Hfin = Wtmp;
+      ldfin = l;
+    }
   }
-  jacobi_sort_kernel<T><<<1, 1024, 0, st>>>(l, H, ldh, W, ldw, dw, dperm);
+  jacobi_sort_kernel<T><<<1, 1024, 0, st>>>(l, Hfin, ldfin, W, ldw, dw, dperm);
   ++nl;
   CHASE_CUDA_TRY(cudaMemcpy2DAsync(Wtmp, sizeof(T) * (size_t)l, W, sizeof(T) * (size_t)ldw,
                                    sizeof(T) * (size_t)l, l, cudaMemcpyDeviceToDevice, st));
@@ -369,8 +448,8 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
 }
 
 template int jacobi_eig<double>(cudaStream_t, int, double*, int, double*, int, double*, void*,
-                                size_t, int, int*, int*);
+                                size_t, int, int*, int*, int);
 template int jacobi_eig<z64>(cudaStream_t, int, z64*, int, z64*, int, double*, void*, size_t, int,
-                             int*, int*);
+                             int*, int*, int);
 
 }  // namespace chase

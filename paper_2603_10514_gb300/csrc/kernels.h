@@ -49,9 +49,10 @@ int householder_qr(cudaStream_t st, int n, int l, T* X, int ldx, T* Vh, int ldv,
 // Returns 5 (CHASE_ERR_TIMEOUT) if a bounded grid-barrier wait ran out.
 constexpr int kJacobiMaxCtas = 1216;  // 8 CTAs of 256 threads on each of the 152 SMs
 size_t jacobi_work_bytes(int l, size_t elem);
+// ctas > 0 fixes the grid size (at most one wave of co-resident CTAs); 0 picks it from l.
 template <class T>
 int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw, void* work,
-               size_t work_bytes, int max_sweeps, int* sweeps, int* launches);
+               size_t work_bytes, int max_sweeps, int* sweeps, int* launches, int ctas = 0);
 
 // ---- streaming kernels (vec.cu) --------------------------------------------
 template <class T>
