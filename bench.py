@@ -51,9 +51,11 @@ BF16_PEAK_TFLOPS, BF16_SUSTAINED_TFLOPS = _measured_peaks()
 # per modulus of the Ozaki scheme II (17 moduli <= 256).
 OZAKI_PAIRS = 17
 # DRAM bytes (read + write) of one emulated product of the default workload (complex
-# n = 10000, 600 active columns) from an ncu capture of the current kernels; None until the
-# capture of these kernels is taken (the line then reports traffic as null).
-OZ_TRAFFIC_PER_LAUNCH = None
+# n = 10000, 600 active columns), measured by one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, 1 pass): the modular-product kernel 15.48 GB read and 0.279 GB
+# written, the CRT kernel 0.300 GB read and 0.076 GB written.  Launches with fewer active
+# columns read the same residue planes of A, which are most of it.
+OZ_TRAFFIC_PER_LAUNCH = 15.48e9 + 0.279e9 + 0.300e9 + 0.076e9
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
@@ -93,6 +95,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=0.0,
                     help="Poisson arrival rate (requests/s); 0 = measure the saturated "
                          "throughput first and use 0.8 of it")
+    ap.add_argument("--caps", default="36,48,64",
+                    help="kappa mode: degree caps of the optimised-degree runs")
     ap.add_argument("--ncols", type=int, default=600, help="filter mode: block width")
     ap.add_argument("--degree", type=int, default=20, help="filter mode: degree of every column")
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "bf16x3"],
@@ -254,8 +258,9 @@ def device_view(ptr, n, ncols, ld, complex_):
 def run_kappa(args):
     """Figure 2 analogue: per iteration, the estimate of Eq. full-est (kappa_est, logged by
     the solver) against the exact kappa_2 of the block [Y V] Algorithm 3 factors (singular
-    values of a host copy, taken through the solver's filtered-block hook), with degree
-    optimisation (first degree 20, cap 36) and without it (degree 20)."""
+    values of a host copy, taken through the solver's filtered-block hook), without degree
+    optimisation (degree 20) and with it (first degree 20, caps from --caps: 36 as in the
+    paper's runs, and higher)."""
     import numpy as np
     import torch
 
@@ -271,7 +276,8 @@ def run_kappa(args):
                                                   W.spectrum_uniform(n, -1, 1, 1)))]:
         A = W.known_spectrum_matrix(prob.lam, prob.seed, prob.complex_, device="cuda")
         V0 = W.start_block(n, prob.ell, prob.seed, prob.complex_)
-        for opt in (False, True):
+        caps = [int(x) for x in args.caps.split(",") if x]
+        for opt, cap in [(False, 36)] + [(True, c) for c in caps]:
             kap = {}
 
             def hook(ptr, nn, ll, ld, it):
@@ -280,7 +286,7 @@ def run_kappa(args):
                 kap[it] = float(sv[0] / sv[-1])
 
             h = P.Handle(0)
-            cfg = P.config_default(opt_degree=int(opt), deg_init=20, deg_max=36,
+            cfg = P.config_default(opt_degree=int(opt), deg_init=20, deg_max=cap,
                                    prec=PRECS[args.prec](P))
             keep = P.with_filtered_hook(cfg, hook)
             Vd = torch.from_numpy(np.ascontiguousarray(V0.T)).cuda().mT
@@ -291,8 +297,13 @@ def run_kappa(args):
                      "log10_kappa_est": g["log_cond_est_paper"] / np.log(10.0),
                      "log10_kappa_est_locked_aware": g["log_cond_est_locked"] / np.log(10.0),
                      "log10_kappa_exact": float(np.log10(kap[g["iteration"]]))} for g in logs]
-            out["runs"].append({"problem": name, "opt": opt, "status": rc,
+            ratio = [r["log10_kappa_est"] - r["log10_kappa_exact"] for r in rows]
+            out["runs"].append({"problem": name, "opt": opt, "deg_max": cap, "status": rc,
                                 "iterations": st["iterations"], "matvecs": st["matvecs"],
+                                "t_total_s": st["t_total"],
+                                "qr_variants": [r["variant"] for r in rows],
+                                "log10_est_over_exact_max": max(ratio) if ratio else None,
+                                "log10_est_over_exact_min": min(ratio) if ratio else None,
                                 "estimate_bounds_exact_before_locking":
                                     all(r["log10_kappa_est"] >= r["log10_kappa_exact"]
                                         for r in rows if r["locked"] == 0),

@@ -106,7 +106,7 @@ struct CrtTable {
   uint32_t C[kOzModuli][5];  // C_j = (P / p_j) ((P / p_j)^{-1} mod p_j) < P
   uint32_t P[5];
   uint32_t Ph[5];            // P / 2
-  double invP;               // 1 / P (rounded)
+  float p96_over_P;          // 2^96 / P (rounded)
 };
 
 constexpr CrtTable make_crt_table() {
@@ -131,7 +131,7 @@ constexpr CrtTable make_crt_table() {
     t.Ph[l] = Ph.w[l];
     pd = pd * 4294967296.0 + (double)P.w[l];
   }
-  t.invP = 1.0 / pd;
+  t.p96_over_P = (float)(79228162514264337593543950336.0 / pd);  // 2^96 / P
   return t;
 }
 
@@ -399,9 +399,11 @@ __device__ __forceinline__ double crt_value(const uint8_t* __restrict__ R, size_
     x[l] = (uint32_t)t;
     carry = t >> 32;
   }
-  // X < 17 * 256 * P < 2^146: reduce mod P with q = floor(X / P) from the top limbs
-  const double xd = ((double)x[4] * 4294967296.0 + (double)x[3]) * 4294967296.0 + (double)x[2];
-  const unsigned int qv = (unsigned int)floor(xd * 18446744073709551616.0 * c_crt.invP);
+  // X < 17 * 256 * P < 2^146: reduce mod P with q = floor(X / P) from the top limbs.  q is
+  // below 2^13, so the FP32 estimate (relative error ~2^-22) is off by at most one; both
+  // corrections follow.
+  const float xf = (float)x[4] * 4294967296.0f + (float)x[3];  // X / 2^96, rounded
+  const unsigned int qv = (unsigned int)floorf(xf * c_crt.p96_over_P);
   {
     unsigned long long borrow = 0, cq = 0;
 #pragma unroll
@@ -489,7 +491,11 @@ __global__ void __launch_bounds__(256) crt_kernel(int M, int N, int splits, cons
     const int r = (int)(t % M), c = (int)(t / M);
     int sh;
     const double x = crt_value(R, stride_z, t, splits, &sh);
-    const double v0 = ldexp(x, sh + rowexp[r] + colexp[col0 + c] - 2 * OZ_KBITS);
+    // x 2^E with |x| in [2^63, 2^64]: one exact multiply by the power of two 2^E built from
+    // its exponent field when that is a normal number (ldexp otherwise)
+    const int E = sh + rowexp[r] + colexp[col0 + c] - 2 * OZ_KBITS;
+    const double v0 = (E > -1022 && E < 1024) ? x * __longlong_as_double((long long)(E + 1023) << 52)
+                                              : ldexp(x, E);
     const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
     double v = alpha * v0;
     if (beta != 0.0) v = fma(beta, X64[idx], v);
