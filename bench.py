@@ -84,11 +84,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=8)
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "filter", "sequence", "serve", "kappa"],
+                    choices=["solve", "filter", "sequence", "serve", "kappa", "batch"],
                     help="solve: the headline time-to-solution; filter: chase_filter alone "
                          "(kernel-level timing and small cases for profilers); sequence: 20 "
                          "correlated real problems with warm starts; serve: a stream of "
-                         "requests through the continuous-batching service")
+                         "requests through the continuous-batching service; batch: many uneven "
+                         "problems in one batch session against one at a time")
+    ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--seq-len", type=int, default=20)
     ap.add_argument("--serve-count", type=int, default=256)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -468,6 +470,73 @@ def cpu_anchor(per_mv_c2, n_c2):
             "s_per_matvec_sampled_at_n%d" % n_c2: per_mv_c2}
 
 
+def run_batch(args):
+    """Many uneven problems at once: `--batch-count` requests of the serving mix (n
+    log-uniform in [500, 4000], real / complex 50/50, nev = 5 % of n, nex = nev / 5, lambda
+    uniform in [-1, 1]) solved by one batch session (their filter steps grouped into shared
+    launches) and, for comparison, one chase_solve after another on the same handle.
+    Inputs resident; CUDA events on the handle's stream; every result checked against the
+    known spectrum."""
+    import numpy as np
+    import torch
+
+    import paper_2603_10514_gb300 as P
+    import workloads as W
+    P.build()
+    specs = W.serving_stream(count=args.batch_count, seed=6, n_lo=500, n_hi=4000)
+    cfg = P.config_default(opt_degree=1, prec=PRECS[args.prec](P))
+    mats = []
+    for s_ in specs:
+        lam = W.spectrum_uniform(s_["n"], -1.0, 1.0, s_["seed"])
+        A = W.known_spectrum_matrix(lam, s_["seed"], s_["complex"], device="cuda")
+        V0 = W.start_block(s_["n"], s_["nev"] + s_["nex"], s_["seed"], s_["complex"])
+        mats.append((s_, lam, A, torch.from_numpy(np.ascontiguousarray(V0.T)).cuda().mT))
+    stream = torch.cuda.current_stream()
+    h = P.Handle(0, stream=stream.cuda_stream)
+
+    def batched():
+        probs = [P.BatchProblem(A, V0.clone(), s_["nev"], s_["nex"],
+                                W.bounds_for(lam, s_["nev"] + s_["nex"]), cfg) for (s_, lam, A, V0) in mats]
+        P.chase_solve_batch(h, probs, cfg)
+        return [(p.status, p.evals, p.resid) for p in probs]
+
+    def one_by_one():
+        out = []
+        for (s_, lam, A, V0) in mats:
+            rc, ev, res, _, _ = P.chase_solve(h, A, V0.clone(), s_["nev"], s_["nex"],
+                                              W.bounds_for(lam, s_["nev"] + s_["nex"]), cfg)
+            out.append((rc, ev, res))
+        return out
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    batched()  # warm-up (workspace pool, code paths)
+    one_by_one()
+    rb, tb = timed(batched)
+    rs, ts = timed(one_by_one)
+    h.close()
+
+    def correct(res):
+        return all(r[0] == 0 and float(np.max(r[2])) < 1e-10 and
+                   float(np.abs(r[1] - lam[:s_["nev"]]).max()) <= 1e-10 * float(np.abs(lam).max())
+                   for r, (s_, lam, _, _) in zip(res, mats))
+
+    same = all(np.array_equal(a[1], b[1]) for a, b in zip(rb, rs))
+    print(json.dumps({"mode": "batch", "prec": args.prec, "problems": len(mats),
+                      "n_range": [min(s_["n"] for s_, _, _, _ in mats), max(s_["n"] for s_, _, _, _ in mats)],
+                      "batched_s": tb, "batched_solves_per_s": len(mats) / tb,
+                      "one_by_one_s": ts, "one_by_one_solves_per_s": len(mats) / ts,
+                      "speedup": ts / tb, "all_correct": correct(rb) and correct(rs),
+                      "batched_equals_single_bitwise": same}), flush=True)
+
+
 def run_reference(args, rank):
     """The oracle arm: the CPU oracle timed on the host cores (rank 0 only).  A complete
     oracle solve of this workload takes hours, so each step times a bounded sample of it
@@ -545,6 +614,9 @@ def main():
         return
     if args.mode == "serve":
         run_serve(args)
+        return
+    if args.mode == "batch":
+        run_batch(args)
         return
     import numpy as np
     import torch

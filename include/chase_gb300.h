@@ -272,6 +272,77 @@ int chase_lanczos_bounds(chase_handle h, chase_dtype dtype, int n, const void* d
                          int nruns, const void* dV0, int ldv, int steps, int ell,
                          chase_bounds* out);
 
+/*
+ * Batches: many eigenproblems advanced together (the batched and serving workloads).
+ *
+ * A batch session keeps any number of problems in flight on one handle and advances every one
+ * of them by one outer iteration of Algorithm 1 per chase_batch_step.  The emulated-FP64 filter
+ * steps (Algorithm 4) of all problems in flight run as shared launches: per step of the
+ * three-term recurrence one slicing, one modular-product and one reconstruction launch over every
+ * problem still filtering (up to 64 problems per launch), so that many small or uneven problems
+ * fill the GPU together.  QR, Rayleigh-Ritz, residuals and locking then run problem by problem.
+ * Each problem's arithmetic is the one chase_solve performs (the grouped products are exact
+ * integer products like the single ones), so results are identical to chase_solve's.  Problems
+ * with other precisions, or with graph_filter = 1, filter one by one inside the same step.
+ * Problems may be added between steps (a service admits requests as earlier ones finish).
+ * Device workspace comes from a caching pool owned by the session.
+ */
+typedef struct chase_batch_ctx* chase_batch;
+
+/* Creates an empty batch session on handle h (its device and stream). */
+int chase_batch_create(chase_batch* b, chase_handle h);
+
+/* Frees the session; problems still in flight are abandoned (their outputs are not written). */
+int chase_batch_destroy(chase_batch b);
+
+/*
+ * chase_batch_add -- arguments as chase_solve; the problem is validated, its workspace taken
+ * from the session's pool, its start block copied, checked and orthonormalised (Algorithm 1's
+ * step 0) before the call returns.  The caller keeps dA, dV and the host outputs (evals, resid,
+ * stats, log) alive until the problem is reported finished by chase_batch_step, which then has
+ * written them as chase_solve would.  *id receives the problem's id in this session.
+ * Returns CHASE_OK, a negative argument index, or an error (nothing added).
+ */
+int chase_batch_add(chase_batch b, chase_dtype dtype, int n, const void* dA, int lda, int nev,
+                    int nex, const chase_config* cfg, const chase_bounds* bounds, void* dV, int ldv,
+                    double* evals, double* resid, chase_stats* stats, chase_iter_log* log,
+                    int log_cap, int* id);
+
+/*
+ * chase_batch_step -- one outer iteration of every problem in flight (if no finished problem is
+ * still waiting to be reported).  Problems that ended -- all nev pairs converged (CHASE_OK),
+ * max_iter reached (CHASE_NOT_CONVERGED) or an error -- are reported in done_ids / done_status
+ * (host arrays of cap entries; *ndone receives the count; more than cap finished problems are
+ * reported by the next calls).
+ */
+int chase_batch_step(chase_batch b, int* done_ids, int* done_status, int cap, int* ndone);
+
+/* Problems in flight plus finished ones not yet reported. */
+int chase_batch_pending(chase_batch b);
+
+/* One problem of chase_solve_batch (arguments as chase_solve's; bounds may be NULL). */
+typedef struct {
+  chase_dtype dtype;
+  int n;
+  const void* dA;
+  int lda;
+  int nev, nex;
+  const chase_bounds* bounds;
+  void* dV;
+  int ldv;
+  double* evals;
+  double* resid;
+  chase_stats* stats; /* may be NULL */
+} chase_problem;
+
+/*
+ * chase_solve_batch -- solves `count` problems through one batch session (every problem added,
+ * then steps until all have ended).  status[i] receives problem i's result (as chase_solve's
+ * return value, or the error its addition met).  Returns CHASE_OK or a session-level error.
+ */
+int chase_solve_batch(chase_handle h, int count, const chase_problem* problems,
+                      const chase_config* cfg, int* status);
+
 /* Static description of a status code. */
 const char* chase_status_string(int status);
 

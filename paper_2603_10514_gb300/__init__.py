@@ -32,7 +32,8 @@ EXPORTED = ["chase_create", "chase_destroy", "chase_config_default", "chase_work
             "chase_solve", "chase_filter", "chase_qr", "chase_qr_prec", "chase_cond_est",
             "chase_status_string",
             "chase_filter_noalloc", "chase_reserve_workspace", "chase_lanczos_bounds",
-            "chase_selftest_wait_timeout"]
+            "chase_selftest_wait_timeout", "chase_batch_create", "chase_batch_destroy",
+            "chase_batch_add", "chase_batch_step", "chase_batch_pending", "chase_solve_batch"]
 
 
 class ChaseError(RuntimeError):
@@ -82,6 +83,13 @@ class IterLog(ctypes.Structure):
                 ("log_cond_est_locked", ctypes.c_double)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("n", ctypes.c_int), ("dA", ctypes.c_void_p),
+                ("lda", ctypes.c_int), ("nev", ctypes.c_int), ("nex", ctypes.c_int),
+                ("bounds", ctypes.c_void_p), ("dV", ctypes.c_void_p), ("ldv", ctypes.c_int),
+                ("evals", ctypes.c_void_p), ("resid", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -114,6 +122,13 @@ def lib():
         L.chase_cond_est.argtypes = [i, i, P, P, d, d, d, d, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.chase_filter_noalloc.argtypes = [i, i, P, i, i, P, i, P, d, d, d, P, i, P]
         L.chase_selftest_wait_timeout.argtypes = [P, d]
+        L.chase_batch_create.argtypes = [ctypes.POINTER(P), P]
+        L.chase_batch_destroy.argtypes = [P]
+        L.chase_batch_pending.argtypes = [P]
+        L.chase_batch_add.argtypes = [P, i, i, P, i, i, i, ctypes.POINTER(Config), ctypes.POINTER(Bounds),
+                                      P, i, P, P, ctypes.POINTER(Stats), P, i, ctypes.POINTER(i)]
+        L.chase_batch_step.argtypes = [P, P, P, i, ctypes.POINTER(i)]
+        L.chase_solve_batch.argtypes = [P, i, P, ctypes.POINTER(Config), P]
         L.chase_status_string.argtypes = [i]
         L.chase_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -334,3 +349,114 @@ def chase_filter_noalloc(A, V, degrees, c, e, lambda1, out=None, stream=None):
     if rc:
         raise ChaseError(rc, "chase_filter_noalloc")
     return out
+
+
+class BatchProblem:
+    """One problem of a batch session: the inputs (kept alive while in flight) and, once the
+    session reports it finished, its results (status, evals, resid, stats)."""
+
+    def __init__(self, A, V, nev, nex, bounds, cfg=None, log_cap=0):
+        self.A, self.V, self.nev, self.nex = A, V, nev, nex
+        self.bounds = Bounds(*[float(x) for x in bounds]) if bounds is not None else None
+        self.cfg = cfg if cfg is not None else config_default()
+        self.evals = np.zeros(nev)
+        self.resid = np.zeros(nev)
+        self._stats = Stats()
+        self.logs = (IterLog * max(1, log_cap))()
+        self.log_cap = log_cap
+        self.status = None
+        self.id = -1
+
+    @property
+    def stats(self):
+        return {f: getattr(self._stats, f) for f, _ in Stats._fields_}
+
+
+class Batch:
+    """A batch session (chase_batch_*): problems in flight advance one outer iteration per
+    step(), their emulated-FP64 filter steps sharing launches.  add() may be called between
+    steps.  step() returns the BatchProblems that ended in that step."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self._b = ctypes.c_void_p()
+        rc = lib().chase_batch_create(ctypes.byref(self._b), handle.ptr)
+        if rc:
+            raise ChaseError(rc, "chase_batch_create")
+        self._live = {}
+
+    def add(self, prob):
+        A, V = prob.A, prob.V
+        dt = _dtype_code(A)
+        if _dtype_code(V) != dt:
+            raise TypeError("A and V must have the same dtype")
+        n = A.shape[0]
+        lda, ldv = _ld(A, "A"), _ld(V, "V")
+        pid = ctypes.c_int(-1)
+        rc = lib().chase_batch_add(self._b, dt, n, ctypes.c_void_p(A.data_ptr()), lda, prob.nev, prob.nex,
+                                   ctypes.byref(prob.cfg),
+                                   ctypes.byref(prob.bounds) if prob.bounds is not None else None,
+                                   ctypes.c_void_p(V.data_ptr()), ldv,
+                                   prob.evals.ctypes.data_as(ctypes.c_void_p),
+                                   prob.resid.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prob._stats),
+                                   ctypes.cast(prob.logs, ctypes.c_void_p), prob.log_cap, ctypes.byref(pid))
+        if rc:
+            raise ChaseError(rc, "chase_batch_add")
+        prob.id = pid.value
+        self._live[prob.id] = prob
+        return prob
+
+    def pending(self):
+        return lib().chase_batch_pending(self._b)
+
+    def step(self):
+        cap = max(1, len(self._live))
+        ids = (ctypes.c_int * cap)()
+        sts = (ctypes.c_int * cap)()
+        nd = ctypes.c_int(0)
+        rc = lib().chase_batch_step(self._b, ctypes.cast(ids, ctypes.c_void_p), ctypes.cast(sts, ctypes.c_void_p),
+                                    cap, ctypes.byref(nd))
+        if rc:
+            raise ChaseError(rc, "chase_batch_step")
+        out = []
+        for j in range(nd.value):
+            prob = self._live.pop(ids[j])
+            prob.status = sts[j]
+            out.append(prob)
+        return out
+
+    def close(self):
+        if self._b:
+            lib().chase_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def chase_solve_batch(h, problems, cfg=None):
+    """Solves the BatchProblems together (chase_solve_batch); fills each one's status,
+    evals, resid and stats."""
+    cfg = cfg if cfg is not None else config_default()
+    arr = (Problem * max(1, len(problems)))()
+    keep = []
+    for i, p in enumerate(problems):
+        A, V = p.A, p.V
+        dt = _dtype_code(A)
+        b = ctypes.pointer(p.bounds) if p.bounds is not None else None
+        keep.append(b)
+        arr[i] = Problem(dt, A.shape[0], A.data_ptr(), _ld(A, "A"), p.nev, p.nex,
+                         ctypes.cast(b, ctypes.c_void_p) if b is not None else None, V.data_ptr(),
+                         _ld(V, "V"), p.evals.ctypes.data, p.resid.ctypes.data,
+                         ctypes.addressof(p._stats))
+    status = (ctypes.c_int * max(1, len(problems)))()
+    rc = lib().chase_solve_batch(h.ptr, len(problems), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(cfg),
+                                 ctypes.cast(status, ctypes.c_void_p))
+    if rc:
+        raise ChaseError(rc, "chase_solve_batch")
+    for i, p in enumerate(problems):
+        p.status = status[i]
+    return [p.status for p in problems]

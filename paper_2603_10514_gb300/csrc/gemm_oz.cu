@@ -223,10 +223,11 @@ __device__ __forceinline__ void ld32(uint32_t taddr, uint32_t* r) {
 // z = split * S + j (grid z).  Lres planes row-major (rows x kp), Vres planes column-major
 // (kp x ncols); both K-padded with zeros to kp (a multiple of 64).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(M_THREADS, 1)
-    ozm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
-               int M, int N, int BN, int col0, int nkb_total, int kbs, uint8_t* __restrict__ R,
-               DevStatus* status) {
+// One CTA's work: rows [m0, m0 + 128) and columns [n0, n0 + BN) of modulus jm over the K
+// blocks [kbeg, kbeg + nkb); residues into Rz (column-major M x N).
+__device__ __forceinline__ void ozm_tile(const CUtensorMap* mapA, const CUtensorMap* mapV, int M,
+                                         int N, int BN, int col0, int m0, int n0, int jm, int kbeg,
+                                         int nkb, uint8_t* __restrict__ Rz, DevStatus* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + MNST * M_STG);
@@ -239,10 +240,6 @@ __global__ void __launch_bounds__(M_THREADS, 1)
   int* s_err = (int*)(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * MBM;
-  const int jm = blockIdx.z % kOzModuli, split = blockIdx.z / kOzModuli;
-  const int kbeg = split * kbs;
-  const int nkb = max(0, min(kbs, nkb_total - kbeg));
   const int nchunks = (nkb + M_CHUNK_KB - 1) / M_CHUNK_KB;
 
   if (threadIdx.x == 0) {
@@ -272,8 +269,8 @@ __global__ void __launch_bounds__(M_THREADS, 1)
       bar_expect(&full[s], bytes);
       unsigned char* st = smem + s * M_STG;
       const int x = (kbeg + kb) * MBK;
-      tma3(st, &mapA, &full[s], x, m0, jm);
-      tma3(st + M_A_T, &mapV, &full[s], x, col0 + n0, jm);
+      tma3(st, mapA, &full[s], x, m0, jm);
+      tma3(st + M_A_T, mapV, &full[s], x, col0 + n0, jm);
       issued = kb + 1;
     }
     for (int b = max(0, issued - MNST); b < issued; ++b)
@@ -348,7 +345,6 @@ __global__ void __launch_bounds__(M_THREADS, 1)
       // sum mod p in [0, p): the float quotient of |sum| < 2^29 is off by at most one
       const int pm = c_crt.p[jm];
       const float ip = 1.0f / (float)pm;
-      uint8_t* Rz = R + (size_t)blockIdx.z * N * M;
 #pragma unroll
       for (int j = 0; j < 64; ++j) {
         const int col = n0 + cq * cw + j;
@@ -371,6 +367,43 @@ __global__ void __launch_bounds__(M_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
   if (threadIdx.x == 32 && *s_err) atomicOr(&status->timeout, *s_err);
+}
+
+__global__ void __launch_bounds__(M_THREADS, 1)
+    ozm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
+               int M, int N, int BN, int col0, int nkb_total, int kbs, uint8_t* __restrict__ R,
+               DevStatus* status) {
+  const int jm = blockIdx.z % kOzModuli, split = blockIdx.z / kOzModuli;
+  const int kbeg = split * kbs;
+  const int nkb = max(0, min(kbs, nkb_total - kbeg));
+  ozm_tile(&mapA, &mapV, M, N, BN, col0, blockIdx.y * MBM, blockIdx.x * BN, jm, kbeg, nkb,
+           R + (size_t)blockIdx.z * N * M, status);
+}
+
+// Grouped products: the tiles of up to kOzGroupMax independent problems in one launch
+// (grid x runs over every problem's tiles, z over the moduli); each problem has its own
+// operands (tensor maps), sizes and residue buffer.  Used to batch the filter steps of many
+// problems.
+struct OzmGroupParams {
+  CUtensorMap mapA[kOzGroupMax];
+  CUtensorMap mapV[kOzGroupMax];
+  uint8_t* R[kOzGroupMax];
+  int tile0[kOzGroupMax + 1];  // first grid-x tile of each problem
+  int M[kOzGroupMax], N[kOzGroupMax], BN[kOzGroupMax], col0[kOzGroupMax], ntile[kOzGroupMax],
+      nkb[kOzGroupMax];
+  int count;
+};
+static_assert(sizeof(OzmGroupParams) <= 32000, "kernel parameter space");
+
+__global__ void __launch_bounds__(M_THREADS, 1)
+    ozm_group_kernel(const __grid_constant__ OzmGroupParams P, DevStatus* status) {
+  int p = 0;
+  while (p + 1 < P.count && (int)blockIdx.x >= P.tile0[p + 1]) ++p;
+  const int t = blockIdx.x - P.tile0[p];
+  const int nt = P.ntile[p];
+  const int jm = blockIdx.z;
+  ozm_tile(&P.mapA[p], &P.mapV[p], P.M[p], P.N[p], P.BN[p], P.col0[p], (t / nt) * MBM,
+           (t % nt) * P.BN[p], jm, 0, P.nkb[p], P.R[p] + (size_t)jm * P.N[p] * P.M[p], status);
 }
 
 // ---------------------------------------------------------------------------
@@ -504,6 +537,46 @@ __global__ void __launch_bounds__(256) crt_kernel(int M, int N, int splits, cons
   }
 }
 
+struct CrtGroupParams {
+  const uint8_t* R[kOzGroupMax];
+  const int* rowexp[kOzGroupMax];
+  const int* colexp[kOzGroupMax];
+  const double* X64[kOzGroupMax];
+  const double* Z64[kOzGroupMax];
+  double* out64[kOzGroupMax];
+  double alpha[kOzGroupMax], beta[kOzGroupMax], gamma[kOzGroupMax];
+  long long out0[kOzGroupMax + 1];  // first output index of each problem
+  int M[kOzGroupMax], N[kOzGroupMax], col0[kOzGroupMax], ldo[kOzGroupMax];
+  int count;
+};
+static_assert(sizeof(CrtGroupParams) <= 32000, "kernel parameter space");
+
+__global__ void __launch_bounds__(256) crt_group_kernel(const __grid_constant__ CrtGroupParams P) {
+  const long long total = P.out0[P.count];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = P.count - 1;  // the problem whose range holds t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.out0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int p = lo;
+    const long long u = t - P.out0[p];
+    const int M = P.M[p];
+    const int r = (int)(u % M), c = (int)(u / M);
+    int sh;
+    const double x = crt_value(P.R[p], (size_t)M * P.N[p], (size_t)u, 1, &sh);
+    const int E = sh + P.rowexp[p][r] + P.colexp[p][P.col0[p] + c] - 2 * OZ_KBITS;
+    const double v0 = (E > -1022 && E < 1024) ? x * __longlong_as_double((long long)(E + 1023) << 52)
+                                              : ldexp(x, E);
+    const size_t idx = (size_t)r + (size_t)(P.col0[p] + c) * P.ldo[p];
+    double v = P.alpha[p] * v0;
+    if (P.beta[p] != 0.0) v = fma(P.beta[p], P.X64[p][idx], v);
+    if (P.gamma[p] != 0.0) v = fma(P.gamma[p], P.Z64[p][idx], v);
+    P.out64[p][idx] = v;
+  }
+}
+
 // ---------------- residues of the integer operands ----------------
 
 // |x| as its IEEE bit pattern: for non-negative doubles the integer order is the numeric
@@ -617,6 +690,38 @@ __global__ void __launch_bounds__(256) oz_slice_V_kernel(int M, int c0, const do
   for (int k = threadIdx.x; k < kp; k += 256) {
     const double x = (k < M) ? col[k] : 0.0;
     write_residues(x, e, planes, (size_t)c * kp + k, plane);
+  }
+}
+
+// Grouped form of oz_slice_V_kernel: one block per sliced column of every problem.
+struct SliceGroupParams {
+  const double* V64[kOzGroupMax];
+  __nv_bfloat16* planes[kOzGroupMax];
+  int* colexp[kOzGroupMax];
+  long long plane[kOzGroupMax];
+  int blk0[kOzGroupMax + 1];  // first block of each problem
+  int M[kOzGroupMax], c0[kOzGroupMax], ldi[kOzGroupMax], kp[kOzGroupMax];
+  int count;
+};
+static_assert(sizeof(SliceGroupParams) <= 32000, "kernel parameter space");
+
+__global__ void __launch_bounds__(256) oz_slice_V_group_kernel(const __grid_constant__ SliceGroupParams P) {
+  __shared__ unsigned long long red[8];
+  int p = 0;
+  while (p + 1 < P.count && (int)blockIdx.x >= P.blk0[p + 1]) ++p;
+  const int c = P.c0[p] + (blockIdx.x - P.blk0[p]);
+  const int M = P.M[p], kp = P.kp[p];
+  const double* col = P.V64[p] + (size_t)c * P.ldi[p];
+  unsigned long long amax = 0;
+  for (int k = threadIdx.x; k < M; k += 256) {
+    const unsigned long long b = abs_bits(col[k]);
+    amax = b > amax ? b : amax;
+  }
+  const int e = exp_bound(block_max(amax, red));
+  if (threadIdx.x == 0) P.colexp[p][c] = e;
+  for (int k = threadIdx.x; k < kp; k += 256) {
+    const double x = (k < M) ? col[k] : 0.0;
+    write_residues(x, e, P.planes[p], (size_t)c * kp + k, (size_t)P.plane[p]);
   }
 }
 
@@ -754,14 +859,15 @@ __global__ void transpose_kernel(int n, int l, const T* __restrict__ X, int ldx,
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // looked up once (thread-safe static initialisation: batch sessions call from several threads)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
     if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
+      return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -843,6 +949,96 @@ int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowe
                                      out64, ldo);
   if (launches) ++*launches;
   CHASE_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int oz_slice_V_group(cudaStream_t st, int count, const OzGroupItem* items, int* launches) {
+  for (int g0 = 0; g0 < count; g0 += kOzGroupMax) {
+    const int cnt = std::min(kOzGroupMax, count - g0);
+    SliceGroupParams P{};
+    int blocks = 0;
+    P.count = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const OzGroupItem& it = items[g0 + i];
+      if (it.N <= 0) continue;
+      const int p = P.count++;
+      P.V64[p] = it.V64_in;
+      P.planes[p] = (__nv_bfloat16*)const_cast<void*>(it.Vplanes);
+      P.colexp[p] = const_cast<int*>(it.colexp);
+      P.plane[p] = (long long)it.ncols_total * it.kp;
+      P.blk0[p] = blocks;
+      P.M[p] = it.M;
+      P.c0[p] = it.col0;
+      P.ldi[p] = it.ldi;
+      P.kp[p] = it.kp;
+      blocks += it.N;
+    }
+    if (P.count == 0) continue;
+    P.blk0[P.count] = blocks;
+    oz_slice_V_group_kernel<<<blocks, 256, 0, st>>>(P);
+    if (launches) ++*launches;
+    CHASE_CUDA_TRY(cudaGetLastError());
+  }
+  return 0;
+}
+
+int oz_gemm_group(cudaStream_t st, int count, const OzGroupItem* items, DevStatus* dst, int* launches) {
+  CHASE_CUDA_TRY(cudaFuncSetAttribute(ozm_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM));
+  for (int g0 = 0; g0 < count; g0 += kOzGroupMax) {
+    const int cnt = std::min(kOzGroupMax, count - g0);
+    OzmGroupParams P{};
+    CrtGroupParams C{};
+    int tiles = 0;
+    long long outs = 0;
+    P.count = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const OzGroupItem& it = items[g0 + i];
+      if (it.N <= 0 || it.M <= 0) continue;
+      if (it.kp % MBK != 0 || it.kp > kOzMaxK) return CHASE_ERR_UNSUPPORTED;
+      if ((size_t)kOzModuli * it.M * it.N > it.resbuf.bytes) return CHASE_ERR_OOM;
+      const int p = P.count++;
+      const int ntile = ceil_div(it.N, MBN_MAX);
+      const int BN = ceil_div(ceil_div(it.N, ntile), 16) * 16;
+      const int rows = std::max(it.a_plane_rows, it.M);
+      if (make_map3(&P.mapA[p], it.Aplanes, it.kp, it.M, rows, MBM) ||
+          make_map3(&P.mapV[p], it.Vplanes, it.kp, it.ncols_total, it.ncols_total, BN))
+        return CHASE_ERR_CUDA;
+      P.R[p] = (uint8_t*)it.resbuf.ptr;
+      P.tile0[p] = tiles;
+      P.M[p] = it.M;
+      P.N[p] = it.N;
+      P.BN[p] = BN;
+      P.col0[p] = it.col0;
+      P.ntile[p] = ntile;
+      P.nkb[p] = it.kp / MBK;
+      tiles += ntile * ceil_div(it.M, MBM);
+      C.R[p] = (const uint8_t*)it.resbuf.ptr;
+      C.rowexp[p] = it.rowexp;
+      C.colexp[p] = it.colexp;
+      C.X64[p] = it.X64;
+      C.Z64[p] = it.Z64;
+      C.out64[p] = it.out64;
+      C.alpha[p] = it.alpha;
+      C.beta[p] = it.beta;
+      C.gamma[p] = it.gamma;
+      C.out0[p] = outs;
+      C.M[p] = it.M;
+      C.N[p] = it.N;
+      C.col0[p] = it.col0;
+      C.ldo[p] = it.ldo;
+      outs += (long long)it.M * it.N;
+    }
+    if (P.count == 0) continue;
+    P.tile0[P.count] = tiles;
+    C.count = P.count;
+    C.out0[C.count] = outs;
+    ozm_group_kernel<<<dim3(tiles, 1, kOzModuli), M_THREADS, M_SMEM, st>>>(P, dst);
+    if (launches) ++*launches;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((outs + 255) / 256, (long long)kNumSMs * 16));
+    crt_group_kernel<<<blocks, 256, 0, st>>>(C);
+    if (launches) ++*launches;
+    CHASE_CUDA_TRY(cudaGetLastError());
+  }
   return 0;
 }
 

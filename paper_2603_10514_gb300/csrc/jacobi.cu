@@ -404,13 +404,15 @@ int jacobi_eig(cudaStream_t st, int l, T* H, int ldh, T* W, int ldw, double* dw,
   if (l > 1) {
     // CTAs: about 2 work items of a round per thread (measured: fewer CTAs leave the FP64
     // work latency-bound, more make the grid barrier dearer), at most one co-resident wave
-    static int max_coresident[2] = {0, 0};
-    int& mc = max_coresident[Sc<T>::cplx ? 1 : 0];
-    if (mc == 0) {
+    // co-resident CTAs of the kernel, looked up once (thread-safe static initialisation)
+    static const int mc = []() {
       int per_sm = 0;
-      CHASE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweeps_kernel<T>, 256, 0));
-      mc = std::max(1, std::min(per_sm * kNumSMs, kJacobiMaxCtas));
-    }
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweeps_kernel<T>, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      return std::max(1, std::min(per_sm * kNumSMs, kJacobiMaxCtas));
+    }();
     const long long items = (long long)(L / 2) * (L / 2) + (long long)l * (L / 2);
     int G = std::max(1, std::min(mc, ceil_div(items, 256 * 2)));
     if (ctas > 0) G = std::min(mc, ctas);

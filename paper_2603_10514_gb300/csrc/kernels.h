@@ -136,6 +136,29 @@ int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowe
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
             DevStatus* dst, Scratch resbuf, int* launches);
 
+// One problem's product in a grouped launch (oz_slice_V_group + oz_gemm_group): the same
+// operands and epilogue as oz_gemm, without K splits; V64_in / ldi: the FP64 stacked block
+// whose columns [col0, col0 + N) oz_slice_V_group cuts into Vplanes first.
+constexpr int kOzGroupMax = 64;  // problems per grouped launch (kernel parameter space)
+struct OzGroupItem {
+  int M = 0, kp = 0, a_plane_rows = 0;
+  const void* Aplanes = nullptr;
+  const int* rowexp = nullptr;
+  const void* Vplanes = nullptr;
+  const int* colexp = nullptr;
+  int ncols_total = 0, col0 = 0, N = 0;
+  double alpha = 1.0, beta = 0.0, gamma = 0.0;
+  const double* X64 = nullptr;
+  const double* Z64 = nullptr;
+  double* out64 = nullptr;
+  int ldo = 0;
+  Scratch resbuf{nullptr, 0};
+  const double* V64_in = nullptr;
+  int ldi = 0;
+};
+int oz_slice_V_group(cudaStream_t st, int count, const OzGroupItem* items, int* launches);
+int oz_gemm_group(cudaStream_t st, int count, const OzGroupItem* items, DevStatus* dst, int* launches);
+
 // ---- failure path of the bounded device waits (selftest.cu) ----------------
 // One thread waits (at most `seconds`) on an mbarrier nothing arrives on and sets
 // dst->timeout, as the kernels do when a wait runs out.

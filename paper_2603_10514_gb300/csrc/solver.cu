@@ -9,11 +9,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "../../include/chase_gb300.h"
@@ -672,97 +675,170 @@ double log_cond_est(double theta_k1, int m_k1, int m_ell, double lambda1, double
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 1
+// Algorithm 1 as a per-problem state advanced one outer iteration at a time:
+// begin (V0 copied, checks, step-0 QR), then per iteration filter() and
+// after_filter() (condition estimate + QR, Rayleigh-Ritz, residuals, locking,
+// next degrees), then finish() (results to the caller).  chase_solve runs one
+// problem through it; a batch session (chase_batch_*) runs many, with the
+// emulated-FP64 filters of all its problems grouped into shared launches.
 // ---------------------------------------------------------------------------
+
+// One problem's part of a grouped emulated-FP64 filter call.
+struct GroupFilterItem {
+  OzBufs* B = nullptr;
+  int ncols = 0;              // unlocked columns filtered
+  const int* deg = nullptr;   // their degrees, ascending
+  double c = 0.0, e = 1.0, lambda1 = 0.0;
+};
+
+struct SolveBase {
+  virtual ~SolveBase() {}
+  virtual int begin() = 0;
+  virtual int filter() = 0;
+  virtual int after_filter() = 0;
+  virtual int finish() = 0;
+  // the iteration's filter may join a grouped launch (emulated FP64, no graph capture)
+  virtual bool group_filter_ok() const = 0;
+  virtual int group_filter_prepare(GroupFilterItem* g) = 0;  // A's residues (once), stacked V
+  virtual int group_filter_done(double seconds, int launches) = 0;  // V back, stats
+  virtual cudaStream_t stream() const = 0;  // where the problem's own work is ordered
+  bool done = false;
+  int status = CHASE_NOT_CONVERGED;  // result once done
+};
+
 template <class T>
-int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const chase_config& cfg,
-               const chase_bounds& bd, T* dV, int ldv, double* evals, double* resid,
-               chase_stats* stats, chase_iter_log* logs, int log_cap) {
-  cudaStream_t st = h->stream;
-  const int l = nev + nex;
-  const Layout L = layout_for<T>(n, l);
-  const bool mixed = (cfg.prec == CHASE_BF16X3);
-  const bool emu = (cfg.prec == CHASE_BF16X3 || cfg.prec == CHASE_FP64_EMU);
-  const size_t tcb_bytes = mixed ? tc_bytes<T>(n, l) : 0;
-  const size_t ozb_bytes = emu ? align256(oz_bytes<T>(n, l)) : 0;
-  TRY(ensure_ws(h, L.total + tcb_bytes + ozb_bytes + (emu ? ozp_bytes<T>(n, l) : 0)));
-  TRY(ensure_hbuf(h, sizeof(double) * 4 * (size_t)l + 4096));
-  char* base = (char*)h->ws;
-  T* V = (T*)(base + L.V);
-  T* P = (T*)(base + L.P);
-  T* AQ = (T*)(base + L.AQ);
-  T* T2 = (T*)(base + L.T2);
-  T* Xs = (T*)(base + L.Xs);
-  T* G = (T*)(base + L.G);
-  T* Ri = (T*)(base + L.Ri);
-  T* H = (T*)(base + L.H);
-  T* Wm = (T*)(base + L.Wm);
-  void* jac = base + L.jac;
-  const size_t jac_bytes = L.dw - L.jac;
-  double* dw = (double*)(base + L.dw);
-  double* dres = (double*)(base + L.dres);
-  Scratch scr{base + L.scratch, kScratchBytes};
+size_t solve_bytes(int n, int l, chase_precision prec) {
+  const bool mixed = (prec == CHASE_BF16X3);
+  const bool emu = (prec == CHASE_BF16X3 || prec == CHASE_FP64_EMU);
+  return layout_for<T>(n, l).total + (mixed ? tc_bytes<T>(n, l) : 0) +
+         (emu ? align256(oz_bytes<T>(n, l)) + ozp_bytes<T>(n, l) : 0);
+}
+
+template <class T>
+struct Solve final : SolveBase {
+  chase_ctx* h;
+  cudaStream_t st;
+  int n, lda, nev, nex, l;
+  const T* A;
+  T* dV;
+  int ldv;
+  chase_config cfg;
+  chase_bounds bd;
+  double* evals;
+  double* resid;
+  chase_stats* stats_out;
+  chase_iter_log* logs;
+  int log_cap;
+  // workspace (solve_bytes) and pinned host staging (4 l doubles)
+  char* base;
+  double* hstage;
+  Layout L;
+  T *V = nullptr, *P = nullptr, *AQ = nullptr, *T2 = nullptr, *Xs = nullptr, *G = nullptr,
+    *Ri = nullptr, *H = nullptr, *Wm = nullptr;
+  void* jac = nullptr;
+  size_t jac_bytes = 0;
+  double *dw = nullptr, *dres = nullptr;
+  Scratch scr{nullptr, 0};
   TcBufs tcb;
-  if (mixed) tcb = tc_carve<T>(base + L.total, n, l);
   OzBufs ozb;
   OzProd ozp;
-  if (emu) {
-    ozb = oz_carve<T>(base + L.total + tcb_bytes, n, l);
-    ozp = ozp_carve<T>(base + L.total + tcb_bytes + ozb_bytes, n, l);
-  }
-  OzProd* ozq = emu ? &ozp : nullptr;
-  bool lowprec = mixed, A_split = false, A_oz = false;
-  const double normA_est = std::max(std::fabs(bd.lambda1), std::fabs(bd.b_sup));
-  double* hw = h->hbuf;        // l Ritz values
-  double* hr = h->hbuf + l;    // l residuals
-
+  OzProd* ozq = nullptr;
+  bool mixed = false, emu = false, lowprec = false, A_split = false, A_oz = false;
+  double normA_est = 0.0;
   chase_stats S{};
-  h->product_timer.collect();  // drop events of an earlier call
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  auto phase_begin = [&]() { cudaEventRecord(e0, st); };
-  auto phase_end = [&](double& acc) {
+  std::vector<int> deg;
+  std::vector<double> ritz, res;
+  double mu1 = 0.0, mu_ell = 0.0, bsup = 0.0;
+  int k = 0, it = 0;
+  long long matvecs = 0;
+  int launches0 = 0;
+  double c = 0.0, e = 1.0;  // the current iteration's damped interval
+  cudaEvent_t e0 = nullptr, e1 = nullptr, t0 = nullptr, t1 = nullptr;
+
+  Solve(chase_ctx* h_, int n_, const T* A_, int lda_, int nev_, int nex_, const chase_config& cfg_,
+        const chase_bounds& bd_, T* dV_, int ldv_, double* evals_, double* resid_,
+        chase_stats* stats_, chase_iter_log* logs_, int log_cap_, char* base_, double* hstage_)
+      : h(h_), st(h_->stream), n(n_), lda(lda_), nev(nev_), nex(nex_), l(nev_ + nex_), A(A_),
+        dV(dV_), ldv(ldv_), cfg(cfg_), bd(bd_), evals(evals_), resid(resid_), stats_out(stats_),
+        logs(logs_), log_cap(log_cap_), base(base_), hstage(hstage_) {}
+
+  ~Solve() override {
+    for (cudaEvent_t ev : {e0, e1, t0, t1})
+      if (ev) cudaEventDestroy(ev);
+  }
+
+  void phase_begin() { cudaEventRecord(e0, st); }
+  void phase_end(double& acc) {
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
     acc += elapsed_s(e0, e1);
-  };
-  cudaEvent_t t0, t1;
-  cudaEventCreate(&t0);
-  cudaEventCreate(&t1);
-  cudaEventRecord(t0, st);
-
-  int rc = 0;
-  const int launches0 = h->launches;
-  std::vector<int> deg(l, cfg.deg_init);
-  std::vector<double> ritz(l, bd.lambda1), res(l, 1.0);
-  std::vector<int> perm(l);
-  double mu1 = bd.lambda1, mu_ell = bd.lambda_ell;
-  const double bsup = bd.b_sup;
-  int k = 0, it = 0, status = CHASE_NOT_CONVERGED;
-  long long matvecs = 0;
-
-  CHASE_CUDA_TRY(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), st));
-  TRY(copy_cols<T>(st, n, l, dV, ldv, V, n, &h->launches));
-  TRY(nonfinite_check<T>(st, n, n, A, lda, h->dstat, &h->launches));
-  TRY(nonfinite_check<T>(st, n, l, V, n, h->dstat, &h->launches));
-  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
-  if (h->hstat->nonfinite) rc = CHASE_ERR_NONFINITE;
-
-  // step 0: orthonormalise V0 (CholeskyQR2; Householder if forced or on failure)
-  if (!rc) {
-    phase_begin();
-    int v0 = 0, fi = 0;
-    rc = qr_dynamic<T>(h, n, l, V, n, std::log(100.0), cfg.cond_hi, cfg.cond_lo,
-                       cfg.qr_force == 4 ? 4 : 0, P, Xs, G, Ri, scr, &v0, &fi, ozq);
-    phase_end(S.t_qr);
   }
 
-  for (it = 0; !rc && it < cfg.max_iter; ++it) {
-    const double c = 0.5 * (bsup + mu_ell), e = 0.5 * (bsup - mu_ell);
+  int begin() override {
+    L = layout_for<T>(n, l);
+    mixed = (cfg.prec == CHASE_BF16X3);
+    emu = (cfg.prec == CHASE_BF16X3 || cfg.prec == CHASE_FP64_EMU);
+    const size_t tcb_bytes = mixed ? tc_bytes<T>(n, l) : 0;
+    const size_t ozb_bytes = emu ? align256(oz_bytes<T>(n, l)) : 0;
+    V = (T*)(base + L.V);
+    P = (T*)(base + L.P);
+    AQ = (T*)(base + L.AQ);
+    T2 = (T*)(base + L.T2);
+    Xs = (T*)(base + L.Xs);
+    G = (T*)(base + L.G);
+    Ri = (T*)(base + L.Ri);
+    H = (T*)(base + L.H);
+    Wm = (T*)(base + L.Wm);
+    jac = base + L.jac;
+    jac_bytes = L.dw - L.jac;
+    dw = (double*)(base + L.dw);
+    dres = (double*)(base + L.dres);
+    scr = Scratch{base + L.scratch, kScratchBytes};
+    if (mixed) tcb = tc_carve<T>(base + L.total, n, l);
+    if (emu) {
+      ozb = oz_carve<T>(base + L.total + tcb_bytes, n, l);
+      ozp = ozp_carve<T>(base + L.total + tcb_bytes + ozb_bytes, n, l);
+      ozq = &ozp;
+    }
+    lowprec = mixed;
+    normA_est = std::max(std::fabs(bd.lambda1), std::fabs(bd.b_sup));
+    for (cudaEvent_t* ev : {&e0, &e1, &t0, &t1})
+      CHASE_CUDA_TRY(cudaEventCreate(ev));
+    cudaEventRecord(t0, st);
+    launches0 = h->launches;
+    deg.assign(l, cfg.deg_init);
+    ritz.assign(l, bd.lambda1);
+    res.assign(l, 1.0);
+    mu1 = bd.lambda1;
+    mu_ell = bd.lambda_ell;
+    bsup = bd.b_sup;
+    CHASE_CUDA_TRY(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), st));
+    TRY(copy_cols<T>(st, n, l, dV, ldv, V, n, &h->launches));
+    TRY(nonfinite_check<T>(st, n, n, A, lda, h->dstat, &h->launches));
+    TRY(nonfinite_check<T>(st, n, l, V, n, h->dstat, &h->launches));
+    CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->hstat->nonfinite) return CHASE_ERR_NONFINITE;
+    // step 0: orthonormalise V0 (CholeskyQR2; Householder if forced or on failure)
+    phase_begin();
+    int v0 = 0, fi = 0;
+    const int rc = qr_dynamic<T>(h, n, l, V, n, std::log(100.0), cfg.cond_hi, cfg.cond_lo,
+                                 cfg.qr_force == 4 ? 4 : 0, P, Xs, G, Ri, scr, &v0, &fi, ozq);
+    phase_end(S.t_qr);
+    if (rc) return rc;
+    if (cfg.max_iter <= 0) done = true;
+    return 0;
+  }
+
+  void interval() {
+    c = 0.5 * (bsup + mu_ell);
+    e = 0.5 * (bsup - mu_ell);
+  }
+
+  int filter() override {
+    interval();
     const int nu = l - k;
-    // --- filter ---
+    int rc = 0;
     phase_begin();
     if (lowprec) {
       double fl = 0.0, tf = 0.0;
@@ -798,7 +874,48 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       phase_end(S.t_filter);
     }
     S.t_filter_product += h->product_timer.collect();  // the phase end synchronised the stream
-    if (rc) break;
+    return rc;
+  }
+
+  bool group_filter_ok() const override { return emu && !lowprec && !cfg.graph_filter; }
+  cudaStream_t stream() const override { return st; }
+
+  int group_filter_prepare(GroupFilterItem* g) override {
+    interval();
+    const int nu = l - k;
+    if (!A_oz) TRY(oz_slice_A<T>(st, n, A, lda, ozb.kp, ozb.Ap, ozb.rowexp, &h->launches));
+    A_oz = true;
+    TRY(oz_stack_V<T>(st, n, nu, V + (size_t)k * n, n, ozb.V64[0], ozb.kp, &h->launches));
+    g->B = &ozb;
+    g->ncols = nu;
+    g->deg = deg.data() + k;
+    g->c = c;
+    g->e = e;
+    g->lambda1 = mu1;
+    return 0;
+  }
+
+  int group_filter_done(double seconds, int launches) override {
+    const int nu = l - k;
+    const int* d = deg.data() + k;
+    int a = 0;
+    while (a < nu) {  // columns ending at an odd step sit in buffer 1, the others in buffer 0
+      int b = a;
+      while (b < nu && d[b] == d[a]) ++b;
+      TRY(tc_unstack_V<T>(st, n, a, b, ozb.V64[d[a] % 2], ozb.kp, V + (size_t)k * n, n,
+                          &h->launches));
+      a = b;
+    }
+    const double per_col = (Sc<T>::cplx ? 8.0 : 2.0) * (double)n * (double)n;
+    for (int j = 0; j < nu; ++j) S.filter_flops += per_col * d[j];
+    S.t_filter += seconds;
+    S.filter_launches += launches;
+    return 0;
+  }
+
+  int after_filter() override {
+    const int nu = l - k;
+    int rc = 0;
     for (int a = k; a < l; ++a) matvecs += deg[a];
     if (cfg.filtered_hook) {
       CHASE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -817,7 +934,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
                                 G, Ri, scr, &variant, &fi, ozq);
     if (!rc && k > 0) rc = copy_cols<T>(st, n, k, T2, n, V, n, &h->launches);
     phase_end(S.t_qr);
-    if (rc) break;
+    if (rc) return rc;
     if (variant == 1) ++S.n_chol1;
     else if (variant == 2) ++S.n_chol2;
     else if (variant == 3) ++S.n_shifted;
@@ -843,7 +960,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     }
     if (!rc) rc = herm_fill_lower<T>(st, nu, H, nu, &h->launches);
     int sweeps = 0;
-    cudaEvent_t j0, j1;
+    cudaEvent_t j0 = nullptr, j1 = nullptr;
     cudaEventCreate(&j0);
     cudaEventCreate(&j1);
     cudaEventRecord(j0, st);
@@ -868,8 +985,10 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       if (!rc) rc = copy_cols<T>(st, n, nu, T2, n, Q2, n, &h->launches);
     }
     phase_end(S.t_rr);
-    if (rc) break;
+    if (rc) return rc;
     // --- residuals (eq. res) ---
+    double* hw = hstage;      // l Ritz values
+    double* hr = hstage + l;  // l residuals
     phase_begin();
     rc = resid_norms<T>(st, n, nu, P, n, Q2, n, dw, dres, &h->launches);
     if (!rc) rc = (cudaMemcpyAsync(hw, dw, sizeof(double) * nu, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
@@ -878,7 +997,7 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
                       ? 0 : CHASE_ERR_CUDA;
     phase_end(S.t_resid);
     if (!rc && h->hstat->timeout) rc = CHASE_ERR_TIMEOUT;
-    if (rc) break;
+    if (rc) return rc;
     for (int a = 0; a < nu; ++a) {
       ritz[k + a] = hw[a];
       res[k + a] = hr[a];
@@ -897,11 +1016,13 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     mu_ell = ritz[l - 1];
     for (int a = k; a < l; ++a) mu_ell = std::max(mu_ell, ritz[a]);
     k = knew;
+    ++it;
     if (k >= nev) {
       status = CHASE_OK;
-      ++it;
-      break;
+      done = true;
+      return 0;
     }
+    if (it >= cfg.max_iter) done = true;  // the next degrees are still formed, as before a filter
     // mixed mode: FP64 filters once the wanted residuals reach the BF16x3 regime
     if (lowprec) {
       double rmax = 0.0;
@@ -930,9 +1051,9 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
       bool moved = false;
       for (int a = 0; a < l - k; ++a) moved |= (idx[a] != k + a);
       if (moved) {
-        std::vector<int> d2(l - k), dd(l - k);
+        std::vector<int> d2(l - k);
         std::vector<double> r2(l - k), s2(l - k);
-        int* hperm = (int*)(h->hbuf + 2 * (size_t)l);
+        int* hperm = (int*)(hstage + 2 * (size_t)l);
         for (int a = 0; a < l - k; ++a) {
           d2[a] = deg[idx[a]]; r2[a] = ritz[idx[a]]; s2[a] = res[idx[a]];
           hperm[a] = idx[a] - k;
@@ -947,42 +1068,338 @@ int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const
     } else {
       for (int a = k; a < l; ++a) deg[a] = cfg.deg_init;
     }
+    return 0;
   }
-  if (rc) {
-    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(t0); cudaEventDestroy(t1);
-    return rc;
+
+  int finish() override {
+    // locked pairs ascending (selection order over the locked prefix)
+    const int kout = std::min(k, nev);
+    std::vector<int> ord(l);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.begin() + kout, [&](int x, int y) { return ritz[x] < ritz[y]; });
+    bool moved = false;
+    for (int a = 0; a < kout; ++a) moved |= (ord[a] != a);
+    if (moved) {
+      int* hperm = (int*)(hstage + 2 * (size_t)l);
+      for (int a = 0; a < l; ++a) hperm[a] = ord[a];
+      int* dperm = (int*)jac;
+      CHASE_CUDA_TRY(cudaMemcpyAsync(dperm, hperm, sizeof(int) * l, cudaMemcpyHostToDevice, st));
+      TRY(copy_cols<T>(st, n, l, V, n, T2, n, &h->launches));
+      TRY(gather_cols<T>(st, n, l, T2, n, dperm, V, n, &h->launches));
+    }
+    TRY(copy_cols<T>(st, n, l, V, n, dV, ldv, &h->launches));
+    cudaEventRecord(t1, st);
+    CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+    S.t_total = elapsed_s(t0, t1);
+    for (int a = 0; a < nev; ++a) {
+      evals[a] = ritz[ord[a]];
+      resid[a] = res[ord[a]];
+    }
+    S.iterations = it;
+    S.locked = k;
+    S.matvecs = matvecs;
+    S.kernel_launches = h->launches - launches0;
+    if (stats_out) *stats_out = S;
+    return status;
   }
-  // locked pairs ascending (selection order over the locked prefix)
-  const int kout = std::min(k, nev);
-  std::vector<int> ord(l);
-  std::iota(ord.begin(), ord.end(), 0);
-  std::stable_sort(ord.begin(), ord.begin() + kout, [&](int x, int y) { return ritz[x] < ritz[y]; });
-  bool moved = false;
-  for (int a = 0; a < kout; ++a) moved |= (ord[a] != a);
-  if (moved) {
-    int* hperm = (int*)(h->hbuf + 2 * (size_t)l);
-    for (int a = 0; a < l; ++a) hperm[a] = ord[a];
-    int* dperm = (int*)jac;
-    CHASE_CUDA_TRY(cudaMemcpyAsync(dperm, hperm, sizeof(int) * l, cudaMemcpyHostToDevice, st));
-    TRY(copy_cols<T>(st, n, l, V, n, T2, n, &h->launches));
-    TRY(gather_cols<T>(st, n, l, T2, n, dperm, V, n, &h->launches));
+};
+
+template <class T>
+int solve_impl(chase_ctx* h, int n, const T* A, int lda, int nev, int nex, const chase_config& cfg,
+               const chase_bounds& bd, T* dV, int ldv, double* evals, double* resid,
+               chase_stats* stats, chase_iter_log* logs, int log_cap) {
+  const int l = nev + nex;
+  TRY(ensure_ws(h, solve_bytes<T>(n, l, cfg.prec)));
+  TRY(ensure_hbuf(h, sizeof(double) * 4 * (size_t)l + 4096));
+  h->product_timer.collect();  // drop events of an earlier call
+  Solve<T> s(h, n, A, lda, nev, nex, cfg, bd, dV, ldv, evals, resid, stats, logs, log_cap,
+             (char*)h->ws, h->hbuf);
+  TRY(s.begin());
+  while (!s.done) {
+    TRY(s.filter());
+    TRY(s.after_filter());
   }
-  TRY(copy_cols<T>(st, n, l, V, n, dV, ldv, &h->launches));
-  cudaEventRecord(t1, st);
-  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
-  S.t_total = elapsed_s(t0, t1);
-  for (int a = 0; a < nev; ++a) {
-    evals[a] = ritz[ord[a]];
-    resid[a] = res[ord[a]];
-  }
-  S.iterations = it;
-  S.locked = k;
-  S.matvecs = matvecs;
-  S.kernel_launches = h->launches - launches0;
-  if (stats) *stats = S;
-  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(t0); cudaEventDestroy(t1);
-  return status;
+  return s.finish();
 }
+
+
+// The emulated-FP64 filters of several problems (Algorithm 4 for each, with its own damped
+// interval, degrees and block) as shared launches: per step of the three-term recurrence one
+// grouped slicing, one grouped modular product and one grouped reconstruction over every
+// problem whose highest degree has not been reached.  Per problem the arithmetic is that of
+// filter_oz (the modular products are exact, so tiling and grouping change no bit).
+int group_filter_oz(chase_ctx* h, const std::vector<SolveBase*>& probs) {
+  cudaStream_t st = h->stream;
+  const int np = (int)probs.size();
+  if (np == 0) return 0;
+  std::vector<GroupFilterItem> g(np);
+  cudaEvent_t a = nullptr, b = nullptr;
+  CHASE_CUDA_TRY(cudaEventCreate(&a));
+  CHASE_CUDA_TRY(cudaEventCreate(&b));
+  // each problem stacks its block (and cuts A's residues once) on its own stream; the shared
+  // launches on this stream wait for all of them
+  for (int p = 0; p < np; ++p) {
+    TRY(probs[p]->group_filter_prepare(&g[p]));
+    if (probs[p]->stream() != st) {
+      cudaEvent_t r = nullptr;
+      CHASE_CUDA_TRY(cudaEventCreateWithFlags(&r, cudaEventDisableTiming));
+      cudaEventRecord(r, probs[p]->stream());
+      cudaStreamWaitEvent(st, r, 0);
+      cudaEventDestroy(r);
+    }
+  }
+  CHASE_CUDA_TRY(cudaMemsetAsync(&h->dstat->timeout, 0, sizeof(int), st));
+  cudaEventRecord(a, st);
+  int launches = 0, rc = 0;
+  std::vector<double> sigma1(np), sigma(np);
+  std::vector<int> first(np, 0);
+  int mmax = 0;
+  for (int p = 0; p < np; ++p) {
+    sigma1[p] = g[p].e / (g[p].lambda1 - g[p].c);
+    sigma[p] = sigma1[p];
+    if (g[p].ncols > 0) mmax = std::max(mmax, g[p].deg[g[p].ncols - 1]);
+  }
+  std::vector<OzGroupItem> items;
+  items.reserve(np);
+  for (int step = 1; step <= mmax && !rc; ++step) {
+    items.clear();
+    for (int p = 0; p < np; ++p) {
+      const GroupFilterItem& q = g[p];
+      if (q.ncols <= 0 || q.deg[q.ncols - 1] < step) continue;
+      while (first[p] < q.ncols && q.deg[first[p]] < step) ++first[p];
+      const int in = (step % 2 == 1) ? 0 : 1, out = 1 - in;
+      double alpha, beta, gamma;
+      if (step == 1) {
+        alpha = sigma1[p] / q.e;
+        beta = -alpha * q.c;
+        gamma = 0.0;
+      } else {
+        const double sn = 1.0 / (2.0 / sigma1[p] - sigma[p]);
+        alpha = 2.0 * sn / q.e;
+        beta = -alpha * q.c;
+        gamma = -sigma[p] * sn;
+        sigma[p] = sn;
+      }
+      const OzBufs& B = *q.B;
+      OzGroupItem it;
+      it.M = B.M;
+      it.kp = B.kp;
+      it.a_plane_rows = B.M;
+      it.Aplanes = B.Ap;
+      it.rowexp = B.rowexp;
+      it.Vplanes = B.Vp;
+      it.colexp = B.colexp;
+      it.ncols_total = q.ncols;
+      it.col0 = first[p];
+      it.N = q.ncols - first[p];
+      it.alpha = alpha;
+      it.beta = beta;
+      it.gamma = gamma;
+      it.X64 = B.V64[in];
+      it.Z64 = B.V64[out];
+      it.out64 = B.V64[out];
+      it.ldo = B.kp;
+      it.resbuf = B.res;
+      it.V64_in = B.V64[in];
+      it.ldi = B.kp;
+      items.push_back(it);
+    }
+    rc = oz_slice_V_group(st, (int)items.size(), items.data(), &launches);
+    if (!rc) rc = oz_gemm_group(st, (int)items.size(), items.data(), h->dstat, &launches);
+  }
+  cudaEventRecord(b, st);
+  const cudaError_t se = cudaEventSynchronize(b);
+  const double t = elapsed_s(a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->launches += launches;
+  if (rc) return rc;
+  if (se != cudaSuccess) return CHASE_ERR_CUDA;
+  for (int p = 0; p < np; ++p) TRY(probs[p]->group_filter_done(t, launches));
+  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h->hstat->timeout) return CHASE_ERR_TIMEOUT;
+  return 0;
+}
+
+// Caching allocator of a batch session: freed blocks stay cached and serve later requests of
+// up to twice their size, so that a service admitting problems of similar shapes allocates
+// (and synchronises the device for cudaFree) rarely.  Device or pinned host memory.
+struct BlockPool {
+  bool host;
+  std::multimap<size_t, void*> cached;
+  size_t cached_bytes = 0;
+  explicit BlockPool(bool host_) : host(host_) {}
+  static size_t round(size_t b) { return (b + ((size_t)2 << 20) - 1) & ~(((size_t)2 << 20) - 1); }
+  void* raw_alloc(size_t b) {
+    void* p = nullptr;
+    const cudaError_t e = host ? cudaMallocHost(&p, b) : cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void raw_free(void* p) {
+    if (host) cudaFreeHost(p);
+    else cudaFree(p);
+  }
+  // returns the block and its (rounded) size in *got; nullptr when the device is full
+  void* get(size_t bytes, size_t* got) {
+    const size_t want = round(bytes);
+    auto it = cached.lower_bound(want);
+    if (it != cached.end() && it->first <= 2 * want) {
+      void* p = it->second;
+      *got = it->first;
+      cached_bytes -= it->first;
+      cached.erase(it);
+      return p;
+    }
+    void* p = raw_alloc(want);
+    if (!p && !cached.empty()) {  // give the cached blocks back and try once more
+      release();
+      p = raw_alloc(want);
+    }
+    *got = want;
+    return p;
+  }
+  void put(void* p, size_t bytes) {
+    if (!p) return;
+    cached.emplace(bytes, p);
+    cached_bytes += bytes;
+  }
+  void release() {
+    for (auto& kv : cached) raw_free(kv.second);
+    cached.clear();
+    cached_bytes = 0;
+  }
+  ~BlockPool() { release(); }
+};
+
+}  // namespace
+
+struct chase_batch_ctx {
+  chase_ctx* h = nullptr;
+  struct Item {
+    int id;
+    SolveBase* s;
+    chase_ctx* sub;  // the problem's own stream and status word
+    void* ws;
+    size_t ws_bytes;
+    double* hst;
+    size_t hst_bytes;
+  };
+  std::vector<Item> items;                       // in flight
+  std::vector<std::pair<int, int>> finished;     // (id, status) not yet reported
+  std::vector<chase_ctx*> subs;                  // idle per-problem contexts
+  int next_id = 0;
+  BlockPool dev{false}, host{true};
+  // A context for one problem: a non-blocking stream and a device status word of its own,
+  // so that the problems' QR and Rayleigh-Ritz phases run concurrently.
+  chase_ctx* get_sub() {
+    if (!subs.empty()) {
+      chase_ctx* c = subs.back();
+      subs.pop_back();
+      return c;
+    }
+    chase_ctx* c = new chase_ctx();
+    c->device = h->device;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc((void**)&c->dstat, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->hstat, sizeof(DevStatus)) != cudaSuccess) {
+      cudaGetLastError();
+      free_sub(c);
+      return nullptr;
+    }
+    c->own_stream = true;
+    return c;
+  }
+  static void free_sub(chase_ctx* c) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->dstat) cudaFree(c->dstat);
+    if (c->hstat) cudaFreeHost(c->hstat);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+  }
+  void release(Item& it) {
+    if (it.sub) cudaStreamSynchronize(it.sub->stream);
+    delete it.s;
+    dev.put(it.ws, it.ws_bytes);
+    host.put(it.hst, it.hst_bytes);
+    if (it.sub) subs.push_back(it.sub);
+    it.s = nullptr;
+    it.sub = nullptr;
+  }
+  ~chase_batch_ctx() {
+    if (h) cudaStreamSynchronize(h->stream);
+    for (Item& it : items) release(it);
+    for (chase_ctx* c : subs) free_sub(c);
+  }
+};
+
+namespace {
+
+// One outer iteration of every problem in flight: the grouped emulated-FP64 filters, the
+// other filters one by one, then each problem's QR, Rayleigh-Ritz, residuals and locking.
+// Problems that end (converged, out of iterations, or failed) are finalised and queued as
+// finished.
+// f(i) for i in [0, n) on up to `threads` host threads (each with the device current).
+template <class F>
+void parallel_for(int n, int device, F f) {
+  const int nt = std::min(n, 16);
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next{0};
+  std::vector<std::thread> pool;
+  pool.reserve(nt);
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&]() {
+      cudaSetDevice(device);
+      for (int i = next++; i < n; i = next++) f(i);
+    });
+  for (std::thread& th : pool) th.join();
+}
+
+void batch_iterate(chase_batch_ctx* b) {
+  const int m = (int)b->items.size();
+  std::vector<SolveBase*> grp;
+  std::vector<int> solo, rcs(m, 0);
+  for (int i = 0; i < m; ++i) {
+    if (b->items[i].s->group_filter_ok()) grp.push_back(b->items[i].s);
+    else solo.push_back(i);
+  }
+  // filters that do not group run on their own streams, concurrently with each other
+  parallel_for((int)solo.size(), b->h->device, [&](int j) { rcs[solo[j]] = b->items[solo[j]].s->filter(); });
+  const int grc = group_filter_oz(b->h, grp);
+  // QR, Rayleigh-Ritz, residuals and locking of every problem, concurrently
+  std::vector<int> ended(m, 0);
+  parallel_for(m, b->h->device, [&](int i) {
+    SolveBase* s = b->items[i].s;
+    int rc = rcs[i];
+    if (!rc && grc && s->group_filter_ok()) rc = grc;
+    if (!rc) rc = s->after_filter();
+    if (!rc && s->done) rc = s->finish();
+    rcs[i] = rc;
+    ended[i] = rc || s->done;
+  });
+  std::vector<chase_batch_ctx::Item> keep;
+  for (int i = 0; i < m; ++i) {
+    chase_batch_ctx::Item& it = b->items[i];
+    if (!ended[i]) {
+      keep.push_back(it);
+      continue;
+    }
+    b->finished.emplace_back(it.id, rcs[i]);
+    b->release(it);
+  }
+  b->items.swap(keep);
+}
+
+}  // namespace
+
+namespace {
 
 template <class T>
 int filter_impl(chase_ctx* h, int n, const T* A, int lda, int ncols, const T* dV, int ldv,
@@ -1293,6 +1710,160 @@ int chase_cond_est(int ell, int nlocked, const double* ritz, const int* degrees,
   const double l = log_cond_est(ritz[nlocked], degrees[nlocked], degrees[ell - 1], lambda1, c, e, eta);
   *est = std::exp(l);
   if (log_est) *log_est = l;
+  return CHASE_OK;
+}
+
+int chase_batch_create(chase_batch* bp, chase_handle h) {
+  if (!bp) return -1;
+  *bp = nullptr;
+  if (!h) return -2;
+  chase_batch_ctx* b = new chase_batch_ctx();
+  b->h = h;
+  *bp = b;
+  return CHASE_OK;
+}
+
+int chase_batch_destroy(chase_batch b) {
+  if (!b) return -1;
+  if (cudaSetDevice(b->h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  delete b;
+  return CHASE_OK;
+}
+
+int chase_batch_pending(chase_batch b) {
+  if (!b) return -1;
+  return (int)(b->items.size() + b->finished.size());
+}
+
+int chase_batch_add(chase_batch b, chase_dtype dtype, int n, const void* dA, int lda, int nev,
+                    int nex, const chase_config* cfg, const chase_bounds* bounds, void* dV, int ldv,
+                    double* evals, double* resid, chase_stats* stats, chase_iter_log* log,
+                    int log_cap, int* id) {
+  if (!b) return -1;
+  if (dtype != CHASE_R64 && dtype != CHASE_C128) return -2;
+  if (n < 1) return -3;
+  if (!dA) return -4;
+  if (lda < n) return -5;
+  if (nev < 1) return -6;
+  if (nex < 0 || nev + nex > n) return -7;
+  chase_config c;
+  if (cfg) c = *cfg; else chase_config_default(&c);
+  if (!(c.tol > 0.0) || c.max_iter < 0 || c.deg_init < 1 || c.deg_min < 1 || c.deg_max < c.deg_min ||
+      !(c.eta > 0.0) || c.qr_force < 0 || c.qr_force > 4 || c.cond_est_mode < 0 ||
+      c.cond_est_mode > 1 || c.graph_filter < 0 || c.graph_filter > 1)
+    return -8;
+  if (c.prec != CHASE_FP64 && c.prec != CHASE_BF16X3 && c.prec != CHASE_FP64_EMU)
+    return CHASE_ERR_UNSUPPORTED;
+  if (c.prec == CHASE_BF16X3 && !(c.mp_switch >= 0.0)) return -8;
+  if (bounds && (!(bounds->b_sup > bounds->lambda_ell) || !(bounds->lambda_ell >= bounds->lambda1)))
+    return -9;
+  if (!dV) return -10;
+  if (ldv < n) return -11;
+  if (!evals) return -12;
+  if (!resid) return -13;
+  if (log_cap < 0) return -16;
+  if (!id) return -17;
+  chase_ctx* h = b->h;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  const int l = nev + nex;
+  chase_bounds bd;
+  if (bounds) {
+    bd = *bounds;
+  } else {
+    if (n < 3) return -9;
+    const int nruns = std::min(4, l), steps = std::min(25, n - 1);
+    const int rc = lanczos_entry(h, dtype, n, dA, lda, nruns, dV, ldv, steps, l, &bd);
+    if (rc) return rc;
+    if (!(bd.b_sup > bd.lambda_ell)) bd.lambda_ell = 0.5 * (bd.lambda1 + bd.b_sup);
+  }
+  chase_batch_ctx::Item it{};
+  const size_t wsb = (dtype == CHASE_R64) ? solve_bytes<double>(n, l, c.prec) : solve_bytes<z64>(n, l, c.prec);
+  it.sub = b->get_sub();
+  if (!it.sub) return CHASE_ERR_CUDA;
+  it.ws = b->dev.get(wsb, &it.ws_bytes);
+  it.hst = (double*)b->host.get(sizeof(double) * 4 * (size_t)l + 4096, &it.hst_bytes);
+  if (!it.ws || !it.hst) {
+    b->release(it);
+    return CHASE_ERR_OOM;
+  }
+  {  // the problem's stream starts after what the caller ordered on the handle's stream
+    cudaEvent_t r = nullptr;
+    if (cudaEventCreateWithFlags(&r, cudaEventDisableTiming) != cudaSuccess) {
+      b->release(it);
+      return CHASE_ERR_CUDA;
+    }
+    cudaEventRecord(r, h->stream);
+    cudaStreamWaitEvent(it.sub->stream, r, 0);
+    cudaEventDestroy(r);
+  }
+  if (dtype == CHASE_R64)
+    it.s = new Solve<double>(it.sub, n, (const double*)dA, lda, nev, nex, c, bd, (double*)dV, ldv,
+                             evals, resid, stats, log, log_cap, (char*)it.ws, it.hst);
+  else
+    it.s = new Solve<z64>(it.sub, n, (const z64*)dA, lda, nev, nex, c, bd, (z64*)dV, ldv, evals,
+                          resid, stats, log, log_cap, (char*)it.ws, it.hst);
+  const int rc = it.s->begin();
+  if (rc) {
+    b->release(it);
+    return rc;
+  }
+  it.id = b->next_id++;
+  *id = it.id;
+  if (it.s->done) {  // max_iter = 0: nothing to iterate
+    b->finished.emplace_back(it.id, it.s->finish());
+    b->release(it);
+    return CHASE_OK;
+  }
+  b->items.push_back(it);
+  return CHASE_OK;
+}
+
+int chase_batch_step(chase_batch b, int* done_ids, int* done_status, int cap, int* ndone) {
+  if (!b) return -1;
+  if (cap < 0 || (cap > 0 && (!done_ids || !done_status))) return -4;
+  if (!ndone) return -5;
+  *ndone = 0;
+  if (cudaSetDevice(b->h->device) != cudaSuccess) return CHASE_ERR_CUDA;
+  if (b->finished.empty() && !b->items.empty()) batch_iterate(b);
+  int m = 0;
+  while (m < cap && !b->finished.empty()) {
+    done_ids[m] = b->finished.front().first;
+    done_status[m] = b->finished.front().second;
+    b->finished.erase(b->finished.begin());
+    ++m;
+  }
+  *ndone = m;
+  return CHASE_OK;
+}
+
+int chase_solve_batch(chase_handle h, int count, const chase_problem* problems,
+                      const chase_config* cfg, int* status) {
+  if (!h) return -1;
+  if (count < 0) return -2;
+  if (count > 0 && !problems) return -3;
+  if (count > 0 && !status) return -5;
+  chase_batch b = nullptr;
+  TRY(chase_batch_create(&b, h));
+  std::vector<int> idx_of(count, -1);
+  std::map<int, int> slot;  // batch id -> problem index
+  for (int i = 0; i < count; ++i) {
+    const chase_problem& p = problems[i];
+    int id = -1;
+    status[i] = chase_batch_add(b, p.dtype, p.n, p.dA, p.lda, p.nev, p.nex, cfg, p.bounds, p.dV,
+                                p.ldv, p.evals, p.resid, p.stats, nullptr, 0, &id);
+    if (status[i] == CHASE_OK) slot[id] = i;
+  }
+  std::vector<int> ids(count + 1), sts(count + 1);
+  while (chase_batch_pending(b) > 0) {
+    int nd = 0;
+    const int rc = chase_batch_step(b, ids.data(), sts.data(), count + 1, &nd);
+    if (rc) {
+      chase_batch_destroy(b);
+      return rc;
+    }
+    for (int j = 0; j < nd; ++j) status[slot[ids[j]]] = sts[j];
+  }
+  chase_batch_destroy(b);
   return CHASE_OK;
 }
 

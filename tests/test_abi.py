@@ -109,7 +109,7 @@ def test_struct_layouts_match_the_header(cl, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     structs = {"chase_config": cl.Config, "chase_stats": cl.Stats, "chase_iter_log": cl.IterLog,
-               "chase_bounds": cl.Bounds}
+               "chase_bounds": cl.Bounds, "chase_problem": cl.Problem}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "chase_gb300.h"',
              "int main(void) {"]
     for cname, py in structs.items():
