@@ -375,13 +375,17 @@ def run_sequence(args):
 def run_serve(args):
     """Serving stream: requests with n log-uniform in [500, 8000], real / complex 50/50,
     nev = 5% of n, nex = nev/5, lambda uniform in [-1, 1], Poisson arrivals at a fixed
-    seed, admitted by HBM footprint onto concurrent solver slots."""
+    seed, admitted by HBM footprint.  Two engines on the same stream: `batch` (the requests
+    in flight share one batch session, their filter steps in shared launches, admitted and
+    completed between outer iterations) and `streams` (whole solves overlapping on
+    concurrent slot handles).  Each engine's saturated rate (all requests at once) is
+    measured; the batch engine is then driven at 0.8 of its saturated rate for latency."""
     import numpy as np
     import torch
 
     import paper_2603_10514_gb300 as P
     import workloads as W
-    from paper_2603_10514_gb300.serve import Request, Server, latency_stats
+    from paper_2603_10514_gb300.serve import BatchServer, Request, Server, latency_stats
     P.build()
     specs = W.serving_stream(count=args.serve_count, seed=5)
     mats = []
@@ -396,11 +400,15 @@ def run_serve(args):
     b = ctypes.c_size_t()
     P.lib().chase_workspace_bytes(P.CHASE_C128, 8000, 400, 80, PRECS[args.prec](P), ctypes.byref(b))
     free, _ = torch.cuda.mem_get_info()
-    budget = int(0.85 * free) - args.serve_slots * b.value
+    budget_streams = int(0.85 * free) - args.serve_slots * b.value
+    budget_batch = int(0.85 * free)
 
-    def run(rate, seed):
-        srv = Server(slots=args.serve_slots, hbm_budget=budget,
-                     make_handle=lambda i: P.Handle(0), slot_workspace=b.value)
+    def run(engine, rate, seed):
+        if engine == "batch":
+            srv = BatchServer(hbm_budget=budget_batch)
+        else:
+            srv = Server(slots=args.serve_slots, hbm_budget=budget_streams,
+                         make_handle=lambda i: P.Handle(0), slot_workspace=b.value)
         rng = np.random.default_rng(seed)
         reqs = []
         t0 = time.perf_counter()
@@ -416,58 +424,26 @@ def run_serve(args):
             reqs.append((srv.submit(req), lam))
         srv.drain()
         wall = time.perf_counter() - t0
-        inflight = srv.max_in_flight
+        inflight = srv.max_seen_in_flight if engine == "batch" else srv.max_in_flight
         srv.close()
         ok = all(r.status == 0 and float(np.max(r.resid)) < 1e-10 and
                  float(np.abs(r.evals - lam[:r.nev]).max()) <= 1e-10 for r, lam in reqs)
         return [r for r, _ in reqs], wall, ok, inflight
 
-    if args.serve_rate > 0:
-        rate = args.serve_rate
-        sat = None
-    else:
-        _, wall_sat, _, _ = run(0.0, 0)
-        sat = len(mats) / wall_sat
-        rate = 0.8 * sat
-    reqs, wall, ok, inflight = run(rate, 5)
-    lat = latency_stats(reqs)
-    print(json.dumps({"mode": "serve", "prec": args.prec, "requests": len(reqs),
-                      "slots": args.serve_slots, "arrival_rate_per_s": rate,
-                      "saturated_solves_per_s": sat, "solves_per_s": len(reqs) / wall,
-                      "wall_s": wall, "latency": lat, "all_correct": ok,
-                      "max_in_flight": inflight}), flush=True)
-
-
-def oracle_full_solve_c1():
-    """One complete oracle solve (Algorithm 1, every step) of the small real workload
-    (n = 1000, nev 20, nex 10, fixed degree 20): the measured anchor of the extrapolated
-    CPU baseline.  Returns seconds, column MatVecs (filter + Rayleigh-Ritz / residual
-    products) and the status."""
-    import oracle
-    import workloads as W
-    prob = W.c1_real_small()
-    A = W.known_spectrum_matrix(prob.lam, prob.seed, False, device="cpu").numpy()
-    V0 = W.start_block(prob.n, prob.ell, prob.seed, False)
-    l1, le, bs = prob.bounds
-    oracle.lib()
-    t0 = time.perf_counter()
-    r = oracle.solve(A, V0, prob.nev, prob.nex, opt_degree=False, deg_init=prob.deg_init,
-                     lambda1=l1, lambda_ell=le, b_sup=bs)
-    dt = time.perf_counter() - t0
-    mv = r["summary"]["matvecs"] + 2 * sum(prob.ell - g["locked_before"] for g in r["logs"])
-    return dt, mv, r["status"], prob.n
-
-
-def cpu_anchor(per_mv_c2, n_c2):
-    """The C1 full solve timed and set beside the C2 sample: the oracle computes in complex
-    arithmetic whatever the input type, so a column MatVec costs ~n^2 work at any size and the
-    C1 per-MatVec time scaled by (n_C2 / n_C1)^2 predicts the C2 sample's."""
-    dt, mv, status, n1 = oracle_full_solve_c1()
-    per_mv_c1 = dt / mv
-    return {"workload": "real symmetric n=%d, nev 20, nex 10, degree 20 (complete oracle solve)" % n1,
-            "solve_s": dt, "status": status, "column_matvecs": mv, "s_per_matvec": per_mv_c1,
-            "s_per_matvec_scaled_to_n%d" % n_c2: per_mv_c1 * (n_c2 / n1) ** 2,
-            "s_per_matvec_sampled_at_n%d" % n_c2: per_mv_c2}
+    out = {"mode": "serve", "prec": args.prec, "requests": len(mats)}
+    sat = {}
+    for engine in ("streams", "batch"):
+        reqs, wall, ok, inflight = run(engine, 0.0, 0)
+        sat[engine] = len(mats) / wall
+        out["saturated_" + engine] = {"solves_per_s": sat[engine], "wall_s": wall, "all_correct": ok,
+                                      "max_in_flight": inflight, "latency": latency_stats(reqs)}
+    rate = args.serve_rate if args.serve_rate > 0 else 0.8 * sat["batch"]
+    reqs, wall, ok, inflight = run("batch", rate, 5)
+    out.update({"engine": "batch", "arrival_rate_per_s": rate, "solves_per_s": len(reqs) / wall,
+                "wall_s": wall, "latency": latency_stats(reqs), "all_correct": ok,
+                "max_in_flight": inflight, "streams_slots": args.serve_slots,
+                "batch_over_streams_saturated": sat["batch"] / sat["streams"]})
+    print(json.dumps(out), flush=True)
 
 
 def run_batch(args):

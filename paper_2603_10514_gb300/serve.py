@@ -1,5 +1,11 @@
 """Continuous-batching eigensolver service on one GPU.
 
+Two engines.  BatchServer (the default one of the benchmark): the requests in flight are
+problems of one batch session, advanced together one outer iteration of Algorithm 1 at a
+time with their filter steps in shared launches; queued requests join between iterations
+as memory frees up, finished ones leave at once.  Server: whole solves on a fixed number
+of concurrent slot handles, described next.
+
 Requests (dense Hermitian / symmetric eigenproblems of different orders) arrive at
 any time.  A request is admitted as soon as a solver slot is idle and its HBM
 footprint fits in the memory left by the requests in flight; admission is
@@ -163,3 +169,135 @@ def latency_stats(reqs):
     lat = np.array([r.t_done - r.t_arrive for r in reqs])
     return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(lat.mean()), "count": int(len(lat))}
+
+
+class BatchServer:
+    """Continuous batching at the granularity of the method's outer iterations: admitted
+    requests live in ONE batch session (chase_batch_*), whose every step advances all of
+    them by one iteration of Algorithm 1 with their filter steps sharing launches (and their
+    QR / Rayleigh-Ritz phases overlapping on per-request streams).  Between steps the
+    scheduler admits queued requests whose device-memory footprint (matrix, search block and
+    solver workspace) fits what the requests in flight leave free -- first come, first
+    served, with backfill past a request that does not fit yet -- and completes the requests
+    that ended.  A request's result is the one chase_solve computes alone (the grouped
+    products are exact integer products; the rest runs per request).
+
+    make_batch() returns the session (default: a Batch on a new handle); `max_in_flight`
+    bounds the requests in one session."""
+
+    def __init__(self, hbm_budget=1 << 62, make_batch=None, workspace_bytes=None, max_in_flight=64):
+        self.budget = hbm_budget
+        self.max_in_flight = max_in_flight
+        self._make_batch = make_batch or self._default_batch
+        self._workspace_bytes = workspace_bytes or self._chase_workspace_bytes
+        self.in_use = 0
+        self.queue = collections.deque()
+        self.cv = threading.Condition()
+        self.closing = False
+        self.completed = []
+        self.max_seen_in_flight = 0
+        self.steps = 0
+        self._handle = None
+        self.sched = threading.Thread(target=self._schedule, daemon=True)
+        self.sched.start()
+
+    # -- defaults (the library) -------------------------------------------------
+    def _default_batch(self):
+        from . import Batch, Handle
+        self._handle = Handle(0)
+        return Batch(self._handle)
+
+    @staticmethod
+    def _chase_workspace_bytes(req):
+        import ctypes
+
+        from . import CHASE_C128, CHASE_R64, config_default, lib
+        cfg = req.cfg if req.cfg is not None else config_default()
+        dt = CHASE_C128 if req.A.element_size() == 16 else CHASE_R64
+        b = ctypes.c_size_t()
+        lib().chase_workspace_bytes(dt, req.n, req.nev, req.nex, cfg.prec, ctypes.byref(b))
+        return int(b.value)
+
+    def footprint(self, req):
+        return req.footprint() + self._workspace_bytes(req)
+
+    # -- client side ----------------------------------------------------------------
+    def submit(self, req: Request):
+        req.t_arrive = time.perf_counter()
+        with self.cv:
+            if self.footprint(req) > self.budget:
+                raise ValueError("request %d needs more memory than the whole budget" % req.rid)
+            self.queue.append(req)
+            self.cv.notify_all()
+        return req
+
+    def drain(self):
+        with self.cv:
+            self.closing = True
+            self.cv.notify_all()
+        self.sched.join()
+
+    def close(self):
+        self.drain()
+        if self._handle is not None:
+            self._handle.close()
+            self._handle = None
+
+    # -- scheduler ------------------------------------------------------------------
+    def _admit(self, batch, live):
+        """Moves queued requests that fit into the session (FCFS with backfill)."""
+        i = 0
+        while i < len(self.queue) and len(live) < self.max_in_flight:
+            req = self.queue[i]
+            fp = self.footprint(req)
+            if self.in_use + fp > self.budget:
+                i += 1
+                continue
+            del self.queue[i]
+            self.in_use += fp
+            req.t_admit = time.perf_counter()
+            req.slot = 0
+            from . import BatchProblem
+            prob = BatchProblem(req.A, req.V0, req.nev, req.nex, req.bounds, req.cfg)
+            try:
+                batch.add(prob)
+            except Exception:  # the request reports the failure, the service carries on
+                self.in_use -= fp
+                self._complete(req, -999, None, None, None)
+                continue
+            live[prob.id] = (req, prob, fp)
+            self.max_seen_in_flight = max(self.max_seen_in_flight, len(live))
+
+    def _complete(self, req, status, evals, resid, stats):
+        req.status, req.evals, req.resid, req.stats = status, evals, resid, stats
+        req.t_done = time.perf_counter()
+        self.completed.append(req)
+        req.done.set()
+
+    def _schedule(self):
+        batch = self._make_batch()
+        live = {}
+        try:
+            while True:
+                with self.cv:
+                    self._admit(batch, live)
+                    if not live:
+                        if self.closing and not self.queue:
+                            return
+                        self.cv.wait(timeout=0.02)
+                        continue
+                try:
+                    finished = batch.step()
+                except Exception:  # a session failure ends every request in it
+                    finished = list(p for (_, p, _) in live.values())
+                    for p in finished:
+                        p.status = -999
+                self.steps += 1
+                with self.cv:
+                    for p in finished:
+                        req, prob, fp = live.pop(p.id)
+                        self.in_use -= fp
+                        self._complete(req, prob.status, prob.evals, prob.resid, prob.stats)
+                    self.cv.notify_all()
+        finally:
+            batch.close()

@@ -108,3 +108,42 @@ def test_service_results_same_alone_and_in_the_mix(cl):
         np.testing.assert_array_equal(req.evals, ev_a)      # bitwise: same kernels, same order
         np.testing.assert_array_equal(req.resid, res_a)
         np.testing.assert_array_equal(req.V0.cpu().numpy(), V_a)
+
+
+def test_batch_service_results_same_alone_and_in_the_mix(cl):
+    """The batch-session service: requests submitted together and while others iterate
+    share one session (their filter steps in shared launches); each result equals the
+    request's solve alone bit for bit."""
+    from paper_2603_10514_gb300.serve import BatchServer
+    specs = [(300, False), (520, True), (410, False), (700, True), (350, True), (610, False),
+             (900, True), (260, False)]
+    reqs = _requests(cl, specs, seed0=90)
+    alone = {}
+    h = cl.Handle(0)
+    try:
+        for req, lam in reqs:
+            V = req.V0.clone()
+            rc, ev, res, st, _ = cl.chase_solve(h, req.A, V, req.nev, req.nex, req.bounds, req.cfg)
+            assert rc == 0 and res.max() < 1e-10
+            assert np.abs(ev - lam[:req.nev]).max() <= 1e-10
+            alone[req.rid] = (ev.copy(), res.copy(), V.cpu().numpy())
+    finally:
+        h.close()
+    srv = BatchServer()
+    try:
+        for req, _ in reqs[:5]:
+            srv.submit(req)
+        import time
+        time.sleep(0.05)  # the rest arrive while the first ones iterate
+        for req, _ in reqs[5:]:
+            srv.submit(req)
+        srv.drain()
+    finally:
+        srv.close()
+    assert srv.max_seen_in_flight >= 2
+    for req, _ in reqs:
+        ev_a, res_a, V_a = alone[req.rid]
+        assert req.status == 0
+        np.testing.assert_array_equal(req.evals, ev_a)
+        np.testing.assert_array_equal(req.resid, res_a)
+        np.testing.assert_array_equal(req.V0.cpu().numpy(), V_a)

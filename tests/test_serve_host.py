@@ -112,3 +112,105 @@ def test_solver_exception_does_not_stall_the_service():
     srv.drain()
     st = {r.rid: r.status for r in srv.completed}
     assert st[1] == -999 and st[0] == st[2] == st[3] == 0
+
+
+# --------------------------------------------------------------------------
+# BatchServer: requests as problems of one batch session, advanced per step
+# --------------------------------------------------------------------------
+
+class FakeBatch:
+    """Stands in for the library's batch session: a problem of order n ends after
+    ceil(n / 500) steps; records how many problems were in flight at every step."""
+
+    def __init__(self):
+        self.live = {}
+        self.next = 0
+        self.inflight = []
+        self.closed = False
+
+    def add(self, prob):
+        prob.id = self.next
+        self.next += 1
+        self.live[prob.id] = [prob, -(-prob.A.shape[0] // 500)]
+        return prob
+
+    def pending(self):
+        return len(self.live)
+
+    def step(self):
+        self.inflight.append(len(self.live))
+        out = []
+        for pid in list(self.live):
+            ent = self.live[pid]
+            ent[1] -= 1
+            if ent[1] == 0:
+                prob = ent[0]
+                prob.status = 0
+                prob.evals = [float(prob.A.shape[0])]
+                out.append(prob)
+                del self.live[pid]
+        time.sleep(0.002)
+        return out
+
+    def close(self):
+        self.closed = True
+
+
+class FakeBatchProblem:
+    def __init__(self, A, V0, nev, nex, bounds, cfg=None):
+        self.A, self.nev, self.nex = A, nev, nex
+        self.status, self.evals, self.resid, self.stats, self.id = None, None, None, None, -1
+
+
+@pytest.fixture
+def fake_problem(monkeypatch):
+    import paper_2603_10514_gb300 as P
+    monkeypatch.setattr(P, "BatchProblem", FakeBatchProblem)
+
+
+def test_batch_server_completes_every_request_within_budget(fake_problem):
+    from paper_2603_10514_gb300.serve import BatchServer
+    reqs = [make(i, n) for i, n in enumerate([500, 3000, 800, 2000, 700, 4000, 600, 1200])]
+    fb = FakeBatch()
+    budget = max(r.footprint() for r in reqs) + 2 * reqs[0].footprint()
+    srv = BatchServer(hbm_budget=budget, make_batch=lambda: fb, workspace_bytes=lambda r: 0,
+                      max_in_flight=3)
+    for r in reqs:
+        srv.submit(r)
+    srv.drain()
+    assert sorted(r.rid for r in srv.completed) == list(range(len(reqs)))
+    assert all(r.status == 0 and r.evals == [float(r.n)] for r in reqs)
+    assert max(fb.inflight) <= 3 and fb.closed
+    assert srv.in_use == 0
+    st = latency_stats(reqs)
+    assert st["count"] == len(reqs) and st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_batch_server_admits_while_others_are_in_flight(fake_problem):
+    """A request arriving while a long one iterates joins the session at the next step
+    (continuous batching) and, being short, finishes first."""
+    from paper_2603_10514_gb300.serve import BatchServer
+    fb = FakeBatch()
+    srv = BatchServer(make_batch=lambda: fb, workspace_bytes=lambda r: 0)
+    long_req = srv.submit(make(0, 20000))
+    time.sleep(0.01)
+    short_req = srv.submit(make(1, 400))
+    srv.drain()
+    assert short_req.t_done < long_req.t_done
+    assert max(fb.inflight) == 2
+
+
+def test_batch_server_backfills_past_a_request_that_does_not_fit(fake_problem):
+    from paper_2603_10514_gb300.serve import BatchServer
+    fb = FakeBatch()
+    big, small = make(0, 3000), make(1, 600)
+    first = make(2, 2800)
+    budget = big.footprint() + small.footprint()  # big fits alone, first + small together
+    srv = BatchServer(hbm_budget=budget, make_batch=lambda: fb, workspace_bytes=lambda r: 0)
+    srv.submit(first)
+    time.sleep(0.01)
+    srv.submit(big)     # does not fit while `first` runs
+    srv.submit(small)   # fits beside `first`: admitted before `big`
+    srv.drain()
+    assert small.t_admit < big.t_admit
+    assert all(r.status == 0 for r in (first, big, small))
