@@ -101,6 +101,9 @@ def parse():
                     help="kappa mode: degree caps of the optimised-degree runs")
     ap.add_argument("--ncols", type=int, default=600, help="filter mode: block width")
     ap.add_argument("--degree", type=int, default=20, help="filter mode: degree of every column")
+    ap.add_argument("--autotune", type=int, default=0, choices=[0, 1],
+                    help="1: the emulated products tune their launch plans during the warm-up "
+                         "solves (chase_config.autotune); the timed solves use the picks")
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "bf16x3"],
                     help="A*V arithmetic: fp64 (DFMA), fp64_emu (Ozaki scheme on the BF16 tensor "
                          "cores, FP64-accurate), bf16x3 (BF16x3 filter while residuals are large, "
@@ -614,7 +617,7 @@ def main():
     h = P.Handle(local, stream=stream.cuda_stream)
     cfg = P.config_default(opt_degree=1, deg_init=prob.deg_init, deg_min=prob.deg_min,
                            deg_max=prob.deg_max, tol=prob.tol,
-                           prec=PRECS[args.prec](P))
+                           prec=PRECS[args.prec](P), autotune=args.autotune)
     bounds = prob.bounds
 
     def one_solve():

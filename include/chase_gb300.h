@@ -107,7 +107,13 @@ typedef struct {
      a default stream (NULL, cudaStreamLegacy, cudaStreamPerThread), otherwise the launches
      are issued directly.  Same kernels in the same order: results are identical.  Default 0. */
   int graph_filter;
-  int reserved[4];
+  /* 1: the emulated-FP64 products tune their launch plans (column-tile width, K splits) the
+     first time the process meets a shape bucket: every candidate plan is timed on that
+     product (the plans give bit-identical results) and the fastest is kept for the process
+     (chase_autotune_table lists the picks).  0 (default): the picks already in the table,
+     else the built-in heuristic. */
+  int autotune;
+  int reserved[3];
 } chase_config;
 
 /* Spectral information the filter needs (Algorithm 1, step "estimate lambda_1,
@@ -137,6 +143,7 @@ typedef struct {
   double t_graph_build;    /* graph_filter = 1: host seconds spent recording and instantiating
                               the filter graphs (inside t_filter) */
   int graph_launches;      /* graph_filter = 1: filter calls that ran as one graph launch */
+  int autotune_trials;     /* autotune = 1: candidate product plans timed during this solve */
 } chase_stats;
 
 /* Per-iteration record (the kind of data Figure 2 plots). */
@@ -275,12 +282,14 @@ int chase_lanczos_bounds(chase_handle h, chase_dtype dtype, int n, const void* d
 /*
  * Batches: many eigenproblems advanced together (the batched and serving workloads).
  *
- * A batch session keeps any number of problems in flight on one handle and advances every one
- * of them by one outer iteration of Algorithm 1 per chase_batch_step.  The emulated-FP64 filter
- * steps (Algorithm 4) of all problems in flight run as shared launches: per step of the
- * three-term recurrence one slicing, one modular-product and one reconstruction launch over every
- * problem still filtering (up to 64 problems per launch), so that many small or uneven problems
- * fill the GPU together.  QR, Rayleigh-Ritz, residuals and locking then run problem by problem.
+ * A batch session keeps any number of problems in flight on one handle.  Each problem has a
+ * stream of its own; its QR, Rayleigh-Ritz, residual and locking phase (Algorithm 1 after the
+ * filter) runs on a worker thread, and as soon as it ends the problem is ready for its next
+ * filter.  The emulated-FP64 filters (Algorithm 4) of all problems ready at that moment run as
+ * shared launches: per step of the three-term recurrence one slicing, one modular-product and
+ * one reconstruction launch over every problem still filtering (up to 64 problems per launch),
+ * so that many small or uneven problems fill the GPU together, and fast problems do not wait
+ * for slow ones.
  * Each problem's arithmetic is the one chase_solve performs (the grouped products are exact
  * integer products like the single ones), so results are identical to chase_solve's.  Problems
  * with other precisions, or with graph_filter = 1, filter one by one inside the same step.
@@ -309,8 +318,10 @@ int chase_batch_add(chase_batch b, chase_dtype dtype, int n, const void* dA, int
                     int log_cap, int* id);
 
 /*
- * chase_batch_step -- one outer iteration of every problem in flight (if no finished problem is
- * still waiting to be reported).  Problems that ended -- all nev pairs converged (CHASE_OK),
+ * chase_batch_step -- advances the problems in flight (if no finished problem is still waiting
+ * to be reported) until every one of them has completed at least one more outer iteration or
+ * ended; faster problems may complete several.  No work of the session runs when it returns.
+ * Calls on one session must not overlap.  Problems that ended -- all nev pairs converged (CHASE_OK),
  * max_iter reached (CHASE_NOT_CONVERGED) or an error -- are reported in done_ids / done_status
  * (host arrays of cap entries; *ndone receives the count; more than cap finished problems are
  * reported by the next calls).
@@ -342,6 +353,16 @@ typedef struct {
  */
 int chase_solve_batch(chase_handle h, int count, const chase_problem* problems,
                       const chase_config* cfg, int* status);
+
+/*
+ * chase_autotune_table -- the autotuner's picks so far (one text line per shape bucket:
+ * shape, bucket, tile-width cap, K splits, measured seconds), NUL-terminated into buf (cap
+ * bytes; truncated if short).  *needed (may be NULL) receives the bytes the full table needs.
+ * chase_autotune_clear -- forgets every pick.  The table is shared by the whole process.
+ * No counterpart in the paper: the launch plans are this implementation's.
+ */
+int chase_autotune_table(char* buf, size_t cap, size_t* needed);
+int chase_autotune_clear(void);
 
 /* Static description of a status code. */
 const char* chase_status_string(int status);

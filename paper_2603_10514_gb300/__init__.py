@@ -33,7 +33,8 @@ EXPORTED = ["chase_create", "chase_destroy", "chase_config_default", "chase_work
             "chase_status_string",
             "chase_filter_noalloc", "chase_reserve_workspace", "chase_lanczos_bounds",
             "chase_selftest_wait_timeout", "chase_batch_create", "chase_batch_destroy",
-            "chase_batch_add", "chase_batch_step", "chase_batch_pending", "chase_solve_batch"]
+            "chase_batch_add", "chase_batch_step", "chase_batch_pending", "chase_solve_batch",
+            "chase_autotune_table", "chase_autotune_clear"]
 
 
 class ChaseError(RuntimeError):
@@ -49,7 +50,7 @@ class Config(ctypes.Structure):
                 ("qr_force", ctypes.c_int), ("prec", ctypes.c_int), ("mp_switch", ctypes.c_double),
                 ("filtered_hook", ctypes.c_void_p), ("filtered_hook_ctx", ctypes.c_void_p),
                 ("cond_est_mode", ctypes.c_int), ("graph_filter", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 FILTERED_HOOK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -70,7 +71,8 @@ class Stats(ctypes.Structure):
                 ("n_lowprec_iters", ctypes.c_int), ("t_filter_lowprec", ctypes.c_double),
                 ("filter_flops_lowprec", ctypes.c_double), ("t_rr_eig", ctypes.c_double),
                 ("jacobi_sweeps", ctypes.c_int), ("t_filter_product", ctypes.c_double),
-                ("t_graph_build", ctypes.c_double), ("graph_launches", ctypes.c_int)]
+                ("t_graph_build", ctypes.c_double), ("graph_launches", ctypes.c_int),
+                ("autotune_trials", ctypes.c_int)]
 
 
 class IterLog(ctypes.Structure):
@@ -129,6 +131,8 @@ def lib():
                                       P, i, P, P, ctypes.POINTER(Stats), P, i, ctypes.POINTER(i)]
         L.chase_batch_step.argtypes = [P, P, P, i, ctypes.POINTER(i)]
         L.chase_solve_batch.argtypes = [P, i, P, ctypes.POINTER(Config), P]
+        L.chase_autotune_table.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        L.chase_autotune_clear.argtypes = []
         L.chase_status_string.argtypes = [i]
         L.chase_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -460,3 +464,16 @@ def chase_solve_batch(h, problems, cfg=None):
     for i, p in enumerate(problems):
         p.status = status[i]
     return [p.status for p in problems]
+
+
+def autotune_table():
+    """The autotuner's picks (chase_autotune_table) as a list of text lines."""
+    need = ctypes.c_size_t(0)
+    lib().chase_autotune_table(None, 0, ctypes.byref(need))
+    buf = ctypes.create_string_buffer(max(1, need.value))
+    lib().chase_autotune_table(buf, len(buf), None)
+    return [ln for ln in buf.value.decode().splitlines() if ln]
+
+
+def autotune_clear():
+    lib().chase_autotune_clear()

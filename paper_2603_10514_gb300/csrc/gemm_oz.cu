@@ -52,6 +52,12 @@
 
 namespace chase {
 
+#define TRY_OZ(x)          \
+  do {                     \
+    int _rc = (x);         \
+    if (_rc) return _rc;   \
+  } while (0)
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -913,15 +919,16 @@ int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ld
   return 0;
 }
 
-int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
-            int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0,
-            int N, double alpha, double beta, const double* X64, double gamma, const double* Z64,
-            double* out64, int ldo, DevStatus* dst, Scratch resbuf, int* launches) {
-  if (N <= 0 || M <= 0) return 0;
-  if (kp % MBK != 0 || kp > kOzMaxK) return CHASE_ERR_UNSUPPORTED;
+namespace {
+
+// The modular products of one plan; returns the number of K splits their residues hold in
+// *splits.
+int ozm_launch(cudaStream_t st, int M, int kp, const void* Aplanes, int a_plane_rows,
+               const void* Vplanes, int ncols_total, int col0, int N, DevStatus* dst,
+               Scratch resbuf, int* launches, const OzPlan& plan, int* splits) {
   if (a_plane_rows < M) a_plane_rows = M;
-  // column tiles of at most 256 (a multiple of 16), as even as possible
-  const int ntile = ceil_div(N, MBN_MAX);
+  // column tiles of at most plan.bn_max (a multiple of 16), as even as possible
+  const int ntile = ceil_div(N, std::min(plan.bn_max, MBN_MAX));
   const int BN = ceil_div(ceil_div(N, ntile), 16) * 16;
   CUtensorMap mA, mV;
   if (make_map3(&mA, Aplanes, kp, M, a_plane_rows, MBM) ||
@@ -934,22 +941,80 @@ int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowe
   // split K (whole 1024-wide chunks) until there are about four waves of CTAs
   const int nchunks = ceil_div(nkb, M_CHUNK_KB);
   int S = std::max(1, std::min(nchunks, ceil_div(4 * kNumSMs, ntile * mblk * kOzModuli)));
+  if (plan.splits > 0) S = std::min(plan.splits, nchunks);
   S = std::min(S, kOzMaxSplits);
   while (S > 1 && (size_t)S * slab > resbuf.bytes) --S;
   if (slab > resbuf.bytes) return CHASE_ERR_OOM;
   const int kbs = ceil_div(nchunks, S) * M_CHUNK_KB;
   S = ceil_div(nkb, kbs);
-  uint8_t* R = (uint8_t*)resbuf.ptr;
   dim3 grid(ntile, mblk, kOzModuli * S);
-  ozm_kernel<<<grid, M_THREADS, M_SMEM, st>>>(mA, mV, M, N, BN, col0, nkb, kbs, R, dst);
+  ozm_kernel<<<grid, M_THREADS, M_SMEM, st>>>(mA, mV, M, N, BN, col0, nkb, kbs, (uint8_t*)resbuf.ptr, dst);
   if (launches) ++*launches;
+  CHASE_CUDA_TRY(cudaGetLastError());
+  *splits = S;
+  return 0;
+}
+
+int crt_launch(cudaStream_t st, int M, int N, int S, Scratch resbuf, const int* rowexp,
+               const int* colexp, int col0, double alpha, double beta, const double* X64,
+               double gamma, const double* Z64, double* out64, int ldo, int* launches) {
   const size_t total = (size_t)M * N;
   const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16));
-  crt_kernel<<<blocks, 256, 0, st>>>(M, N, S, R, rowexp, colexp, col0, alpha, beta, X64, gamma, Z64,
-                                     out64, ldo);
+  crt_kernel<<<blocks, 256, 0, st>>>(M, N, S, (const uint8_t*)resbuf.ptr, rowexp, colexp, col0, alpha,
+                                     beta, X64, gamma, Z64, out64, ldo);
   if (launches) ++*launches;
   CHASE_CUDA_TRY(cudaGetLastError());
   return 0;
+}
+
+}  // namespace
+
+int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
+            int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0,
+            int N, double alpha, double beta, const double* X64, double gamma, const double* Z64,
+            double* out64, int ldo, DevStatus* dst, Scratch resbuf, int* launches, int tune,
+            int* trials) {
+  if (N <= 0 || M <= 0) return 0;
+  if (kp % MBK != 0 || kp > kOzMaxK) return CHASE_ERR_UNSUPPORTED;
+  OzPlan plan;
+  const bool known = oz_plan_lookup(M, N, kp, &plan);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (tune && !known && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
+      cs == cudaStreamCaptureStatusNone) {
+    // time the modular products of every candidate plan (they read only the residue planes
+    // and all yield the same exact residues), keep the fastest, then run it once more and
+    // reconstruct: the three-term update, which may read its own output, runs once
+    OzPlan cand[6];
+    const int nc = oz_plan_candidates(N, cand, 6);
+    cudaEvent_t ev[7];
+    for (int i = 0; i <= nc; ++i) CHASE_CUDA_TRY(cudaEventCreate(&ev[i]));
+    int rc = 0, S = 1;
+    cudaEventRecord(ev[0], st);
+    for (int i = 0; i < nc && !rc; ++i) {
+      rc = ozm_launch(st, M, kp, Aplanes, a_plane_rows, Vplanes, ncols_total, col0, N, dst, resbuf,
+                      launches, cand[i], &S);
+      cudaEventRecord(ev[i + 1], st);
+    }
+    if (!rc && cudaEventSynchronize(ev[nc]) == cudaSuccess) {
+      int best = 0;
+      float tbest = 1e30f;
+      for (int i = 0; i < nc; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+        if (ms < tbest) { tbest = ms; best = i; }
+      }
+      oz_plan_store(M, N, kp, cand[best], tbest * 1e-3);
+      if (trials) *trials += nc;
+      plan = cand[best];
+    }
+    for (int i = 0; i <= nc; ++i) cudaEventDestroy(ev[i]);
+    if (rc) return rc;
+  }
+  int S = 1;
+  TRY_OZ(ozm_launch(st, M, kp, Aplanes, a_plane_rows, Vplanes, ncols_total, col0, N, dst, resbuf,
+                    launches, plan, &S));
+  return crt_launch(st, M, N, S, resbuf, rowexp, colexp, col0, alpha, beta, X64, gamma, Z64, out64,
+                    ldo, launches);
 }
 
 int oz_slice_V_group(cudaStream_t st, int count, const OzGroupItem* items, int* launches) {
@@ -997,7 +1062,9 @@ int oz_gemm_group(cudaStream_t st, int count, const OzGroupItem* items, DevStatu
       if (it.kp % MBK != 0 || it.kp > kOzMaxK) return CHASE_ERR_UNSUPPORTED;
       if ((size_t)kOzModuli * it.M * it.N > it.resbuf.bytes) return CHASE_ERR_OOM;
       const int p = P.count++;
-      const int ntile = ceil_div(it.N, MBN_MAX);
+      OzPlan plan;  // the autotuner's tile width for this shape, if it measured one
+      oz_plan_lookup(it.M, it.N, it.kp, &plan);
+      const int ntile = ceil_div(it.N, std::min(plan.bn_max, MBN_MAX));
       const int BN = ceil_div(ceil_div(it.N, ntile), 16) * 16;
       const int rows = std::max(it.a_plane_rows, it.M);
       if (make_map3(&P.mapA[p], it.Aplanes, it.kp, it.M, rows, MBM) ||

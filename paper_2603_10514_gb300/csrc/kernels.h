@@ -127,14 +127,27 @@ template <class T>
 int oz_gram_assemble(cudaStream_t st, int l, const double* out, int ldo, T* G, int ldg, int* launches);
 template <class T>
 int transpose(cudaStream_t st, int n, int l, const T* X, int ldx, T* Xt, int ldt, int* launches);
+// Launch plan of an emulated product: cap on the column-tile width (tiles as even as
+// possible below it) and K splits (0: about four waves of CTAs, at most kOzMaxSplits).
+struct OzPlan {
+  int bn_max = 256;
+  int splits = 0;
+};
+// The autotuner's table (autotune.cu): plans measured per shape bucket.
+bool oz_plan_lookup(int M, int N, int kp, OzPlan* plan);
+void oz_plan_store(int M, int N, int kp, const OzPlan& plan, double seconds);
+int oz_plan_candidates(int N, OzPlan* out, int cap);
 // out64[:, col0 + c] = alpha * (A V)[:, col0 + c] + beta * X64 + gamma * Z64 for c < N.
 // A's planes are a_plane_rows * kp elements apart (0: M * kp).  resbuf: residues of the
 // modular products, at least oz_residue_bytes(M, N) / kOzMaxSplits bytes (twice that lets
-// the product split K).  kp must be a multiple of 64 and at most kOzMaxK.
+// the product split K).  kp must be a multiple of 64 and at most kOzMaxK.  The plan is the
+// autotuner's pick for the shape's bucket if it has one, else the heuristic; tune = 1 first
+// measures every candidate plan on this product (unless the stream is being captured) and
+// records the fastest; *trials counts the candidate runs.
 int oz_gemm(cudaStream_t st, int M, int kp, const void* Aplanes, const int* rowexp,
             int a_plane_rows, const void* Vplanes, const int* colexp, int ncols_total, int col0, int N, double alpha,
             double beta, const double* X64, double gamma, const double* Z64, double* out64, int ldo,
-            DevStatus* dst, Scratch resbuf, int* launches);
+            DevStatus* dst, Scratch resbuf, int* launches, int tune = 0, int* trials = nullptr);
 
 // One problem's product in a grouped launch (oz_slice_V_group + oz_gemm_group): the same
 // operands and epilogue as oz_gemm, without K splits; V64_in / ldi: the FP64 stacked block

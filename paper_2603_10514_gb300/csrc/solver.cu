@@ -12,6 +12,9 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -82,6 +85,8 @@ struct chase_ctx {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int launches = 0;
   LaunchTimer product_timer;  // filter product launches of the current solve / call
+  int autotune = 0;           // 1: emulated products tune their launch plans (autotune.cu)
+  int tune_trials = 0;        // candidate plans run by the tuner during the current solve
 };
 
 namespace {
@@ -384,7 +389,8 @@ int filter_oz_enqueue(chase_ctx* h, int n, const T* A, int lda, bool split_A, in
     TRY(oz_slice_V(st, M, first, ncols, B.V64[in], kp, kp, ncols, B.Vp, B.colexp, &h->launches));
     h->product_timer.begin(st);
     TRY(oz_gemm(st, M, kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, ncols, first, act, alpha, beta,
-                B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, B.res, &h->launches));
+                B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, B.res, &h->launches,
+                h->autotune, &h->tune_trials));
     h->product_timer.end(st);
     if (flops) *flops += per_col * act;
     if (steps) ++*steps;
@@ -470,7 +476,8 @@ int aq_oz(chase_ctx* h, int n, const T* Q, int nu, T* AQ, OzBufs& B, Scratch scr
   TRY(oz_stack_V<T>(st, n, nu, Q, n, B.V64[0], B.kp, &h->launches));
   TRY(oz_slice_V(st, B.M, 0, nu, B.V64[0], B.kp, B.kp, B.ncols, B.Vp, B.colexp, &h->launches));
   TRY(oz_gemm(st, B.M, B.kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, B.ncols, 0, nu, 1.0, 0.0, nullptr,
-              0.0, nullptr, B.V64[1], B.kp, h->dstat, B.res, &h->launches));
+              0.0, nullptr, B.V64[1], B.kp, h->dstat, B.res, &h->launches, h->autotune,
+              &h->tune_trials));
   TRY(tc_unstack_V<T>(st, n, 0, nu, B.V64[1], B.kp, AQ, n, &h->launches));
   return 0;
 }
@@ -552,7 +559,7 @@ int oz_gram(chase_ctx* h, OzProd& P, int q, const T* X, int ldx, const T* Y, int
     plane_rows = q;
   }
   TRY(oz_gemm(st, q, P.kp, left, lexp, plane_rows, P.Gp, P.gexp, wq, 0, wq, 1.0, 0.0, nullptr, 0.0,
-              nullptr, P.out, q, h->dstat, P.res, &h->launches));
+              nullptr, P.out, q, h->dstat, P.res, &h->launches, h->autotune, &h->tune_trials));
   TRY(oz_gram_assemble<T>(st, q, P.out, q, G, ldg, &h->launches));
   return 0;
 }
@@ -577,7 +584,7 @@ int oz_tall(chase_ctx* h, OzProd& P, int kl, const T* X, int ldx, int N, T* Y, i
   TRY(transpose<T>(st, P.n, kl, X, ldx, Xt, kl, &h->launches));
   TRY(oz_slice_rows<T>(st, P.n, kl, Xt, kl, P.kpl, P.Rp, P.rexp, &h->launches));
   TRY(oz_gemm(st, P.M, P.kpl, P.Rp, P.rexp, 0, P.Bp, P.bexp, N, 0, N, 1.0, 0.0, nullptr, 0.0,
-              nullptr, P.out, P.M, h->dstat, P.res, &h->launches));
+              nullptr, P.out, P.M, h->dstat, P.res, &h->launches, h->autotune, &h->tune_trials));
   TRY(tc_unstack_V<T>(st, P.n, 0, N, P.out, P.M, Y, ldy, &h->launches));
   return 0;
 }
@@ -802,6 +809,8 @@ struct Solve final : SolveBase {
     }
     lowprec = mixed;
     normA_est = std::max(std::fabs(bd.lambda1), std::fabs(bd.b_sup));
+    h->autotune = cfg.autotune;
+    h->tune_trials = 0;
     for (cudaEvent_t* ev : {&e0, &e1, &t0, &t1})
       CHASE_CUDA_TRY(cudaEventCreate(ev));
     cudaEventRecord(t0, st);
@@ -1099,6 +1108,7 @@ struct Solve final : SolveBase {
     S.locked = k;
     S.matvecs = matvecs;
     S.kernel_launches = h->launches - launches0;
+    S.autotune_trials = h->tune_trials;
     if (stats_out) *stats_out = S;
     return status;
   }
@@ -1343,47 +1353,112 @@ namespace {
 // other filters one by one, then each problem's QR, Rayleigh-Ritz, residuals and locking.
 // Problems that end (converged, out of iterations, or failed) are finalised and queued as
 // finished.
-// f(i) for i in [0, n) on up to `threads` host threads (each with the device current).
-template <class F>
-void parallel_for(int n, int device, F f) {
-  const int nt = std::min(n, 16);
-  if (nt <= 1) {
-    for (int i = 0; i < n; ++i) f(i);
-    return;
-  }
-  std::atomic<int> next{0};
-  std::vector<std::thread> pool;
-  pool.reserve(nt);
-  for (int t = 0; t < nt; ++t)
-    pool.emplace_back([&]() {
-      cudaSetDevice(device);
-      for (int i = next++; i < n; i = next++) f(i);
-    });
-  for (std::thread& th : pool) th.join();
-}
-
-void batch_iterate(chase_batch_ctx* b) {
+// One chase_batch_step: the problems in flight advance asynchronously.  Worker threads run
+// each problem's phase after its filter (QR, Rayleigh-Ritz, residuals, locking -- or, for a
+// problem that does not group, its own filter first) on the problem's stream; as soon as a
+// problem's phase ends it is ready for its next filter, and the calling thread launches one
+// grouped emulated-FP64 filter for every problem ready at that moment.  Fast problems thus
+// do not wait for slow ones, and the grouped launches take whoever is ready.  The call
+// returns once every problem in flight has advanced at least one outer iteration (or ended),
+// with no phase running: problems can then be added before the next call.
+void batch_advance(chase_batch_ctx* b) {
   const int m = (int)b->items.size();
-  std::vector<SolveBase*> grp;
-  std::vector<int> solo, rcs(m, 0);
-  for (int i = 0; i < m; ++i) {
-    if (b->items[i].s->group_filter_ok()) grp.push_back(b->items[i].s);
-    else solo.push_back(i);
+  if (m == 0) return;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<int> tasks;
+  std::vector<int> done_idx;  // indices whose phase finished, not yet collected
+  std::vector<int> rc(m, 0), ended(m, 0), adv(m, 0), solo(m, 0);
+  int running = 0;
+  bool quit = false;
+  const int nw = std::min(m, 16);
+  std::vector<std::thread> workers;
+  workers.reserve(nw);
+  for (int w = 0; w < nw; ++w)
+    workers.emplace_back([&]() {
+      cudaSetDevice(b->h->device);
+      for (;;) {
+        int i;
+        {
+          std::unique_lock<std::mutex> lk(mu);
+          cv.wait(lk, [&] { return quit || !tasks.empty(); });
+          if (tasks.empty()) return;
+          i = tasks.front();
+          tasks.pop_front();
+        }
+        SolveBase* s = b->items[i].s;
+        int r = 0;
+        if (solo[i]) r = s->filter();
+        if (!r) r = s->after_filter();
+        if (!r && s->done) r = s->finish();
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          rc[i] = r;
+          ended[i] = (r != 0) || s->done;
+          done_idx.push_back(i);
+          --running;
+        }
+        cv.notify_all();
+      }
+    });
+  std::vector<int> ready(m);
+  std::iota(ready.begin(), ready.end(), 0);
+  bool stopping = false;
+  for (;;) {
+    if (!stopping && !ready.empty()) {
+      std::vector<SolveBase*> grp;
+      std::vector<int> gi;
+      for (int i : ready) {
+        solo[i] = !b->items[i].s->group_filter_ok();
+        if (!solo[i]) {
+          grp.push_back(b->items[i].s);
+          gi.push_back(i);
+        }
+      }
+      const int grc = group_filter_oz(b->h, grp);  // phases of other problems run meanwhile
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int i : ready) {
+          if (!solo[i] && grc) {  // the shared filter failed: the problem ends with that error
+            rc[i] = grc;
+            ended[i] = 1;
+            done_idx.push_back(i);
+            continue;
+          }
+          tasks.push_back(i);
+          ++running;
+        }
+      }
+      cv.notify_all();
+      ready.clear();
+    }
+    std::vector<int> got;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait(lk, [&] { return !done_idx.empty() || (running == 0 && tasks.empty()); });
+      got.swap(done_idx);
+    }
+    for (int i : got) {
+      if (ended[i]) continue;
+      ++adv[i];
+      if (!stopping) ready.push_back(i);
+    }
+    if (!stopping) {
+      bool all = true;
+      for (int i = 0; i < m; ++i) all = all && (ended[i] || adv[i] >= 1);
+      stopping = all;
+    }
+    if (stopping) {
+      std::unique_lock<std::mutex> lk(mu);
+      if (running == 0 && tasks.empty() && done_idx.empty()) break;
+    }
   }
-  // filters that do not group run on their own streams, concurrently with each other
-  parallel_for((int)solo.size(), b->h->device, [&](int j) { rcs[solo[j]] = b->items[solo[j]].s->filter(); });
-  const int grc = group_filter_oz(b->h, grp);
-  // QR, Rayleigh-Ritz, residuals and locking of every problem, concurrently
-  std::vector<int> ended(m, 0);
-  parallel_for(m, b->h->device, [&](int i) {
-    SolveBase* s = b->items[i].s;
-    int rc = rcs[i];
-    if (!rc && grc && s->group_filter_ok()) rc = grc;
-    if (!rc) rc = s->after_filter();
-    if (!rc && s->done) rc = s->finish();
-    rcs[i] = rc;
-    ended[i] = rc || s->done;
-  });
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    quit = true;
+  }
+  cv.notify_all();
+  for (std::thread& t : workers) t.join();
   std::vector<chase_batch_ctx::Item> keep;
   for (int i = 0; i < m; ++i) {
     chase_batch_ctx::Item& it = b->items[i];
@@ -1391,7 +1466,7 @@ void batch_iterate(chase_batch_ctx* b) {
       keep.push_back(it);
       continue;
     }
-    b->finished.emplace_back(it.id, rcs[i]);
+    b->finished.emplace_back(it.id, rc[i]);
     b->release(it);
   }
   b->items.swap(keep);
@@ -1591,7 +1666,8 @@ int chase_solve(chase_handle h, chase_dtype dtype, int n, const void* dA, int ld
   if (cfg) c = *cfg; else chase_config_default(&c);
   if (!(c.tol > 0.0) || c.max_iter < 0 || c.deg_init < 1 || c.deg_min < 1 || c.deg_max < c.deg_min ||
       !(c.eta > 0.0) || c.qr_force < 0 || c.qr_force > 4 || c.cond_est_mode < 0 ||
-      c.cond_est_mode > 1 || c.graph_filter < 0 || c.graph_filter > 1)
+      c.cond_est_mode > 1 || c.graph_filter < 0 || c.graph_filter > 1 || c.autotune < 0 ||
+      c.autotune > 1)
     return -8;
   if (c.prec != CHASE_FP64 && c.prec != CHASE_BF16X3 && c.prec != CHASE_FP64_EMU)
     return CHASE_ERR_UNSUPPORTED;
@@ -1750,7 +1826,8 @@ int chase_batch_add(chase_batch b, chase_dtype dtype, int n, const void* dA, int
   if (cfg) c = *cfg; else chase_config_default(&c);
   if (!(c.tol > 0.0) || c.max_iter < 0 || c.deg_init < 1 || c.deg_min < 1 || c.deg_max < c.deg_min ||
       !(c.eta > 0.0) || c.qr_force < 0 || c.qr_force > 4 || c.cond_est_mode < 0 ||
-      c.cond_est_mode > 1 || c.graph_filter < 0 || c.graph_filter > 1)
+      c.cond_est_mode > 1 || c.graph_filter < 0 || c.graph_filter > 1 || c.autotune < 0 ||
+      c.autotune > 1)
     return -8;
   if (c.prec != CHASE_FP64 && c.prec != CHASE_BF16X3 && c.prec != CHASE_FP64_EMU)
     return CHASE_ERR_UNSUPPORTED;
@@ -1824,7 +1901,7 @@ int chase_batch_step(chase_batch b, int* done_ids, int* done_status, int cap, in
   if (!ndone) return -5;
   *ndone = 0;
   if (cudaSetDevice(b->h->device) != cudaSuccess) return CHASE_ERR_CUDA;
-  if (b->finished.empty() && !b->items.empty()) batch_iterate(b);
+  if (b->finished.empty() && !b->items.empty()) batch_advance(b);
   int m = 0;
   while (m < cap && !b->finished.empty()) {
     done_ids[m] = b->finished.front().first;

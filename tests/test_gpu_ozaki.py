@@ -218,3 +218,36 @@ def test_qr_prec_rejects_other_precisions(cl, handle):
     Xd = dev(W.gaussian((50, 5), 1, False))
     rc, v, info = cl.chase_qr(handle, Xd, 1.0, prec=cl.CHASE_TF32, check=False)
     assert rc == -9
+
+
+def test_autotuner_records_plans_without_changing_results(cl):
+    """autotune = 1: the first solve times the candidate launch plans of its emulated
+    products (trials > 0) and records the fastest per shape bucket; the results equal an
+    untuned solve's bit for bit (every plan forms the same exact integer products); a second
+    tuned solve of the same shapes finds every bucket in the table (no trials)."""
+    prob = W.c2_complex_clustered(n=1100, nev=40, nex=12, seed=19)
+    A_t = W.known_spectrum_matrix(prob.lam, prob.seed, True, device="cuda")
+    V0 = W.start_block(prob.n, prob.ell, prob.seed, True)
+    cl.autotune_clear()
+    out = []
+    for tune in (0, 1, 1):
+        h = cl.Handle(0)
+        try:
+            cfg = cl.config_default(opt_degree=1, prec=cl.CHASE_FP64_EMU, autotune=tune)
+            V = dev(V0)
+            rc, ev, res, st, _ = cl.chase_solve(h, A_t, V, prob.nev, prob.nex, prob.bounds, cfg)
+        finally:
+            h.close()
+        assert rc == 0
+        out.append((ev, res, V.cpu().numpy(), st))
+    assert out[0][3]["autotune_trials"] == 0
+    assert out[1][3]["autotune_trials"] > 0
+    assert out[2][3]["autotune_trials"] == 0
+    for i in (1, 2):
+        np.testing.assert_array_equal(out[i][0], out[0][0])
+        np.testing.assert_array_equal(out[i][1], out[0][1])
+        np.testing.assert_array_equal(out[i][2], out[0][2])
+    table = cl.autotune_table()
+    assert table and all(ln.startswith("ozm ") and "tile_cap=" in ln for ln in table)
+    cl.autotune_clear()
+    assert cl.autotune_table() == []
