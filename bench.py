@@ -52,10 +52,10 @@ BF16_PEAK_TFLOPS, BF16_SUSTAINED_TFLOPS = _measured_peaks()
 OZAKI_PAIRS = 17
 # DRAM bytes (read + write) of one emulated product of the default workload (complex
 # n = 10000, 600 active columns), measured by one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, 1 pass): the modular-product kernel 15.48 GB read and 0.279 GB
-# written, the CRT kernel 0.300 GB read and 0.076 GB written.  Launches with fewer active
-# columns read the same residue planes of A, which are most of it.
-OZ_TRAFFIC_PER_LAUNCH = 15.48e9 + 0.279e9 + 0.300e9 + 0.076e9
+# dram__bytes_write.sum, 1 pass) of the CTA-pair modular-product kernel: 15.68 GB read and
+# 0.268 GB written; the CRT kernel 0.300 GB read and 0.076 GB written.  Launches with fewer
+# active columns read the same residue planes of A, which are most of it.
+OZ_TRAFFIC_PER_LAUNCH = 15.676e9 + 0.268e9 + 0.300e9 + 0.076e9
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
@@ -447,6 +447,38 @@ def run_serve(args):
                 "max_in_flight": inflight, "streams_slots": args.serve_slots,
                 "batch_over_streams_saturated": sat["batch"] / sat["streams"]})
     print(json.dumps(out), flush=True)
+
+
+def oracle_full_solve_c1():
+    """One complete oracle solve (Algorithm 1, every step) of the small real workload
+    (n = 1000, nev 20, nex 10, fixed degree 20): the measured anchor of the extrapolated
+    CPU baseline.  Returns seconds, column MatVecs (filter + Rayleigh-Ritz / residual
+    products) and the status."""
+    import oracle
+    import workloads as W
+    prob = W.c1_real_small()
+    A = W.known_spectrum_matrix(prob.lam, prob.seed, False, device="cpu").numpy()
+    V0 = W.start_block(prob.n, prob.ell, prob.seed, False)
+    l1, le, bs = prob.bounds
+    oracle.lib()
+    t0 = time.perf_counter()
+    r = oracle.solve(A, V0, prob.nev, prob.nex, opt_degree=False, deg_init=prob.deg_init,
+                     lambda1=l1, lambda_ell=le, b_sup=bs)
+    dt = time.perf_counter() - t0
+    mv = r["summary"]["matvecs"] + 2 * sum(prob.ell - g["locked_before"] for g in r["logs"])
+    return dt, mv, r["status"], prob.n
+
+
+def cpu_anchor(per_mv_c2, n_c2):
+    """The C1 full solve timed and set beside the C2 sample: the oracle computes in complex
+    arithmetic whatever the input type, so a column MatVec costs ~n^2 work at any size and the
+    C1 per-MatVec time scaled by (n_C2 / n_C1)^2 predicts the C2 sample's."""
+    dt, mv, status, n1 = oracle_full_solve_c1()
+    per_mv_c1 = dt / mv
+    return {"workload": "real symmetric n=%d, nev 20, nex 10, degree 20 (complete oracle solve)" % n1,
+            "solve_s": dt, "status": status, "column_matvecs": mv, "s_per_matvec": per_mv_c1,
+            "s_per_matvec_scaled_to_n%d" % n_c2: per_mv_c1 * (n_c2 / n1) ** 2,
+            "s_per_matvec_sampled_at_n%d" % n_c2: per_mv_c2}
 
 
 def run_batch(args):
