@@ -99,6 +99,44 @@ struct DevStatus {
   int pad;
 };
 
+#ifdef __CUDACC__
+// Grid-wide barrier of a cooperative launch on a counter that only grows: barrier k ends
+// once all G CTAs have added their arrival (count >= (k + 1) G).  One release-add per CTA
+// and acquire polls with a short back-off.  Bounded: returns false (the caller leaves the
+// kernel) when the wait ran out or another CTA gave up.
+struct GridBar {
+  unsigned count;
+  int abort;
+  int sweeps;
+  int pad;
+};
+constexpr long long kBarWait = 2000000000LL;  // ~1 s of clock64
+
+__device__ inline bool grid_barrier(GridBar* gb, unsigned nblocks, unsigned& k) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (nblocks == 1) return true;  // one CTA: the block barrier orders its global writes
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = (++k) * nblocks;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->count) : "memory");
+    const long long t0 = clock64();
+    while (true) {
+      unsigned c;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(&gb->count) : "memory");
+      if ((int)(c - target) >= 0) break;
+      if (*(volatile int*)&gb->abort) { ok = 0; break; }
+      if (clock64() - t0 > kBarWait) { atomicExch(&gb->abort, 1); ok = 0; break; }
+      __nanosleep(20);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+#endif
+
 }  // namespace chase
 
 #define CHASE_CUDA_TRY(expr)                         \

@@ -915,13 +915,14 @@ __global__ void __launch_bounds__(512) oz_slice_cols_kernel(int n, int q, const 
 
 // out (l x 2l FP64, ld ldo) -> G (l x l, ld ldg) with G = out[:, :l] + i out[:, l:] (real: copy)
 template <class T>
-__global__ void gram_assemble_kernel(int l, const double* __restrict__ out, int ldo, T* G, int ldg) {
-  const size_t total = (size_t)l * l;
+__global__ void gram_assemble_kernel(int qx, int qy, const double* __restrict__ out, int ldo, T* G,
+                                     int ldg) {
+  const size_t total = (size_t)qx * qy;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
-    const int p = (int)(t % l), q = (int)(t / l);
+    const int p = (int)(t % qx), q = (int)(t / qx);
     if constexpr (Sc<T>::cplx) {
-      G[(size_t)p + (size_t)q * ldg] = z64{out[(size_t)p + (size_t)q * ldo], out[(size_t)p + (size_t)(q + l) * ldo]};
+      G[(size_t)p + (size_t)q * ldg] = z64{out[(size_t)p + (size_t)q * ldo], out[(size_t)p + (size_t)(q + qy) * ldo]};
     } else {
       G[(size_t)p + (size_t)q * ldg] = out[(size_t)p + (size_t)q * ldo];
     }
@@ -1246,10 +1247,12 @@ int oz_slice_cols(cudaStream_t st, int n, int q, const T* Y, int ldy, int kp, bo
 }
 
 template <class T>
-int oz_gram_assemble(cudaStream_t st, int l, const double* out, int ldo, T* G, int ldg, int* launches) {
-  const size_t work = (size_t)l * l;
+int oz_gram_assemble(cudaStream_t st, int qx, int qy, const double* out, int ldo, T* G, int ldg,
+                     int* launches) {
+  const size_t work = (size_t)qx * qy;
+  if (work == 0) return 0;
   const int blocks = (int)std::max<size_t>(1, std::min<size_t>((work + 255) / 256, (size_t)kNumSMs * 16));
-  gram_assemble_kernel<T><<<blocks, 256, 0, st>>>(l, out, ldo, G, ldg);
+  gram_assemble_kernel<T><<<blocks, 256, 0, st>>>(qx, qy, out, ldo, G, ldg);
   if (launches) ++*launches;
   CHASE_CUDA_TRY(cudaGetLastError());
   return 0;
@@ -1268,7 +1271,7 @@ int transpose(cudaStream_t st, int n, int l, const T* X, int ldx, T* Xt, int ldt
   template int oz_slice_rows<T>(cudaStream_t, int, int, const T*, int, int, void*, int*, int*);   \
   template int oz_slice_cols<T>(cudaStream_t, int, int, const T*, int, int, bool, void*, int*,   \
                                 int*);                                                            \
-  template int oz_gram_assemble<T>(cudaStream_t, int, const double*, int, T*, int, int*);         \
+  template int oz_gram_assemble<T>(cudaStream_t, int, int, const double*, int, T*, int, int*);    \
   template int transpose<T>(cudaStream_t, int, int, const T*, int, T*, int, int*);
 OZ_INST(double)
 OZ_INST(z64)

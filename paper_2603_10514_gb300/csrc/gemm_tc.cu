@@ -319,17 +319,19 @@ __global__ void split_V_kernel(int n, int ncols, const T* __restrict__ V, int ld
 // Stacked FP64 columns [c0, c1) back into the caller's layout.
 template <class T>
 __global__ void unstack_V_kernel(int n, int c0, int c1, const double* __restrict__ V64, int ldi,
-                                 T* V, int ldv) {
+                                 T* V, int ldv, bool subtract) {
   const size_t total = (size_t)n * (c1 - c0);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(t % n), a = c0 + (int)(t / n);
+    T u;
     if constexpr (Sc<T>::cplx) {
-      V[(size_t)i + (size_t)a * ldv] =
-          z64{V64[(size_t)i + (size_t)a * ldi], V64[(size_t)(i + n) + (size_t)a * ldi]};
+      u = z64{V64[(size_t)i + (size_t)a * ldi], V64[(size_t)(i + n) + (size_t)a * ldi]};
     } else {
-      V[(size_t)i + (size_t)a * ldv] = V64[(size_t)i + (size_t)a * ldi];
+      u = V64[(size_t)i + (size_t)a * ldi];
     }
+    T* d = V + (size_t)i + (size_t)a * ldv;
+    *d = subtract ? Sc<T>::sub(*d, u) : u;
   }
 }
 
@@ -393,9 +395,10 @@ int tc_split_V(cudaStream_t st, int n, int ncols, const T* V, int ldv, double* V
 
 template <class T>
 int tc_unstack_V(cudaStream_t st, int n, int c0, int c1, const double* V64, int ldi, T* V, int ldv,
-                 int* launches) {
+                 int* launches, bool subtract) {
   if (c1 <= c0) return 0;
-  unstack_V_kernel<T><<<grid_for((size_t)n * (c1 - c0)), 256, 0, st>>>(n, c0, c1, V64, ldi, V, ldv);
+  unstack_V_kernel<T><<<grid_for((size_t)n * (c1 - c0)), 256, 0, st>>>(n, c0, c1, V64, ldi, V, ldv,
+                                                                      subtract);
   if (launches) ++*launches;
   CHASE_CUDA_TRY(cudaGetLastError());
   return 0;
@@ -429,7 +432,7 @@ template int tc_split_V<double>(cudaStream_t, int, int, const double*, int, doub
 template int tc_split_V<z64>(cudaStream_t, int, int, const z64*, int, double*, int, int, void*,
                              void*, int*);
 template int tc_unstack_V<double>(cudaStream_t, int, int, int, const double*, int, double*, int,
-                                  int*);
-template int tc_unstack_V<z64>(cudaStream_t, int, int, int, const double*, int, z64*, int, int*);
+                                  int*, bool);
+template int tc_unstack_V<z64>(cudaStream_t, int, int, int, const double*, int, z64*, int, int*, bool);
 
 }  // namespace chase

@@ -41,6 +41,22 @@ int trtri_upper(cudaStream_t st, int n, const T* R, int ldr, T* Rinv, int ldri, 
 template <class T>
 int householder_qr(cudaStream_t st, int n, int l, T* X, int ldx, T* Vh, int ldv, double* dnorm,
                    int* launches);
+// Blocked form's pieces: reflectors j0 .. j0+b-1 into Vh[:, j0..] applied within the panel
+// only; the compact WY factor T (b x b, ld ldt) from G = V^H V; X <- [I; 0] (n x l).
+template <class T>
+int hh_panel(cudaStream_t st, int n, int j0, int b, T* X, int ldx, T* Vh, int ldv, int* launches);
+// The panel step as one cooperative launch (rows split over up to 152 CTAs, two bounded
+// grid barriers per column), which also writes the panel Gram V^H V (upper, ld ldg).
+// CHASE_ERR_UNSUPPORTED when the grid cannot be co-resident or a slice is too tall (the
+// caller then takes hh_panel and a product for the Gram); a wait that ran out sets
+// dst->timeout.  Scratch: at least 256 + (b + b(b+1)/2) * 1216 elements.
+template <class T>
+int hh_panel_coop(cudaStream_t st, int n, int j0, int b, T* X, int ldx, T* Vh, int ldv, T* Gp, int ldg,
+                  Scratch ws, DevStatus* dst, int* launches);
+template <class T>
+int hh_build_T(cudaStream_t st, int b, const T* G, int ldg, T* Tm, int ldt, int* launches);
+template <class T>
+int hh_thin_identity(cudaStream_t st, int n, int l, T* X, int ldx, int* launches);
 
 // ---- parallel cyclic Jacobi eigensolver (jacobi.cu) ------------------------
 // Diagonalises the Hermitian H (l x l, overwritten).  Eigenvalues (ascending)
@@ -85,9 +101,11 @@ int tc_split_A(cudaStream_t st, int n, const T* A, int lda, int kp, void* Ah, vo
 template <class T>
 int tc_split_V(cudaStream_t st, int n, int ncols, const T* V, int ldv, double* V64, int ldo, int kp,
                void* Vh, void* Vl, int* launches);
+// V[:, c0:c1] = unstack(V64) (complex: rows i and n + i of V64 are the real and imaginary
+// parts); with subtract, V[:, c0:c1] -= unstack(V64).
 template <class T>
 int tc_unstack_V(cudaStream_t st, int n, int c0, int c1, const double* V64, int ldi, T* V, int ldv,
-                 int* launches);
+                 int* launches, bool subtract = false);
 // One filter step on columns [col0, col0 + N) of the stacked block (ld kp everywhere).
 int tc_filter_step(cudaStream_t st, int M, int kp, const void* Ah, const void* Al,
                    const void* Vh_in, const void* Vl_in, int ncols_total, int col0, int N,
@@ -122,9 +140,11 @@ int oz_slice_rows(cudaStream_t st, int n, int l, const T* Xt, int ldt, int kp, v
 template <class T>
 int oz_slice_cols(cudaStream_t st, int n, int q, const T* Y, int ldy, int kp, bool pair,
                   void* planes, int* colexp, int* launches);
-// G = out[:, :l] + i out[:, l:] (complex) or out (real); out l x 2l (or l x l), ld ldo.
+// G = out[:, :qy] + i out[:, qy:] (complex) or out (real); out qx x 2qy (or qx x qy), ld ldo;
+// G qx x qy.
 template <class T>
-int oz_gram_assemble(cudaStream_t st, int l, const double* out, int ldo, T* G, int ldg, int* launches);
+int oz_gram_assemble(cudaStream_t st, int qx, int qy, const double* out, int ldo, T* G, int ldg,
+                     int* launches);
 template <class T>
 int transpose(cudaStream_t st, int n, int l, const T* X, int ldx, T* Xt, int ldt, int* launches);
 // Launch plan of an emulated product: cap on the column-tile width (tiles as even as

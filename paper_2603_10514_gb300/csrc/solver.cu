@@ -560,32 +560,52 @@ int oz_gram(chase_ctx* h, OzProd& P, int q, const T* X, int ldx, const T* Y, int
   }
   TRY(oz_gemm(st, q, P.kp, left, lexp, plane_rows, P.Gp, P.gexp, wq, 0, wq, 1.0, 0.0, nullptr, 0.0,
               nullptr, P.out, q, h->dstat, P.res, &h->launches, h->autotune, &h->tune_trials));
-  TRY(oz_gram_assemble<T>(st, q, P.out, q, G, ldg, &h->launches));
+  TRY(oz_gram_assemble<T>(st, q, q, P.out, q, G, ldg, &h->launches));
   return 0;
 }
 
-// Digit planes of the small right factor B (kl x N, ld ldb) for oz_tall.
+// Digit planes of the small right factor B (kl x N, ld ldb) for oz_tall.  kpk: padded K of
+// the product (0: the whole block's, P.kpl; a narrower factor passes tc_kpad of its own K so
+// that the modular products do not run over zero padding).
 template <class T>
-int oz_prep_factor(chase_ctx* h, OzProd& P, int kl, int N, const T* B, int ldb) {
+int oz_prep_factor(chase_ctx* h, OzProd& P, int kl, int N, const T* B, int ldb, int kpk = 0) {
   cudaStream_t st = h->stream;
   const int K = Sc<T>::cplx ? 2 * kl : kl;
-  TRY(oz_stack_V<T>(st, kl, N, B, ldb, P.B64, P.kpl, &h->launches));
-  TRY(oz_slice_V(st, K, 0, N, P.B64, P.kpl, P.kpl, N, P.Bp, P.bexp, &h->launches));
+  if (kpk <= 0) kpk = P.kpl;
+  TRY(oz_stack_V<T>(st, kl, N, B, ldb, P.B64, kpk, &h->launches));
+  TRY(oz_slice_V(st, K, 0, N, P.B64, kpk, kpk, N, P.Bp, P.bexp, &h->launches));
   return 0;
 }
 
-// Y = X B (n x N, ld ldy) with X n x kl (ld ldx) and B prepared by oz_prep_factor.
-// Y may alias X: X is fully sliced before Y is written.
+// Y = X B (n x N, ld ldy), or Y -= X B with subtract, with X n x kl (ld ldx) and B prepared
+// by oz_prep_factor with the same kpk.  Y may alias X: X is fully sliced before Y is written.
 template <class T>
-int oz_tall(chase_ctx* h, OzProd& P, int kl, const T* X, int ldx, int N, T* Y, int ldy, Scratch scr) {
+int oz_tall(chase_ctx* h, OzProd& P, int kl, const T* X, int ldx, int N, T* Y, int ldy, Scratch scr,
+            int kpk = 0, bool subtract = false) {
   cudaStream_t st = h->stream;
   if (N <= 0) return 0;
+  if (kpk <= 0) kpk = P.kpl;
   T* Xt = (T*)P.Xt;
   TRY(transpose<T>(st, P.n, kl, X, ldx, Xt, kl, &h->launches));
-  TRY(oz_slice_rows<T>(st, P.n, kl, Xt, kl, P.kpl, P.Rp, P.rexp, &h->launches));
-  TRY(oz_gemm(st, P.M, P.kpl, P.Rp, P.rexp, 0, P.Bp, P.bexp, N, 0, N, 1.0, 0.0, nullptr, 0.0,
+  TRY(oz_slice_rows<T>(st, P.n, kl, Xt, kl, kpk, P.Rp, P.rexp, &h->launches));
+  TRY(oz_gemm(st, P.M, kpk, P.Rp, P.rexp, 0, P.Bp, P.bexp, N, 0, N, 1.0, 0.0, nullptr, 0.0,
               nullptr, P.out, P.M, h->dstat, P.res, &h->launches, h->autotune, &h->tune_trials));
-  TRY(tc_unstack_V<T>(st, P.n, 0, N, P.out, P.M, Y, ldy, &h->launches));
+  TRY(tc_unstack_V<T>(st, P.n, 0, N, P.out, P.M, Y, ldy, &h->launches, subtract));
+  return 0;
+}
+
+// W = X^H Y (qx x qy, ld ldw) for X n x qx and Y n x qy (the rectangular form of oz_gram).
+template <class T>
+int oz_xhy(chase_ctx* h, OzProd& P, int qx, const T* X, int ldx, int qy, const T* Y, int ldy, T* W,
+           int ldw) {
+  cudaStream_t st = h->stream;
+  if (qx <= 0 || qy <= 0) return 0;
+  const int wqy = Sc<T>::cplx ? 2 * qy : qy;
+  TRY(oz_slice_cols<T>(st, P.n, qy, Y, ldy, P.kp, true, P.Gp, P.gexp, &h->launches));
+  TRY(oz_slice_cols<T>(st, P.n, qx, X, ldx, P.kp, false, P.Lp, P.lexp, &h->launches));
+  TRY(oz_gemm(st, qx, P.kp, P.Lp, P.lexp, qx, P.Gp, P.gexp, wqy, 0, wqy, 1.0, 0.0, nullptr, 0.0,
+              nullptr, P.out, qx, h->dstat, P.res, &h->launches, h->autotune, &h->tune_trials));
+  TRY(oz_gram_assemble<T>(st, qx, qy, P.out, qx, W, ldw, &h->launches));
   return 0;
 }
 
@@ -623,6 +643,79 @@ int cholqr_pass(chase_ctx* h, int n, int l, T* X, int ldx, T* Xtmp, T* G, T* Ri,
   return 0;
 }
 
+// C <- (I - V op(T) V^H) C, op(T) = T^H (trans) or T, for the panel's reflectors V (n x b,
+// ld n; zero above row j0) and a block C (n x nc, ld ldc; rows above j0 are left as they
+// are, since V vanishes there).  W, W2: b x nc (ld b).
+template <class T>
+int wy_apply(chase_ctx* h, int n, int j0, int b, const T* V, const T* Tm, int ldt, bool trans, T* C,
+             int ldc, int nc, T* W, T* W2, Scratch scr, OzProd* oz) {
+  cudaStream_t st = h->stream;
+  if (nc <= 0) return 0;
+  if (oz)
+    TRY(oz_xhy<T>(h, *oz, b, V, n, nc, C, ldc, W, b));
+  else
+    TRY(gemm<T>(st, true, b, nc, n - j0, V + j0, n, C + j0, ldc, W, b, 1.0, 0.0, nullptr, 0, 0.0,
+                nullptr, 0, scr, false, false, &h->launches));
+  TRY(gemm<T>(st, trans, b, nc, b, Tm, ldt, W, b, W2, b, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, scr,
+              false, false, &h->launches));
+  if (oz) {
+    const int kpk = tc_kpad(Sc<T>::cplx ? 2 * b : b);
+    TRY(oz_prep_factor<T>(h, *oz, b, nc, W2, b, kpk));
+    TRY(oz_tall<T>(h, *oz, b, V, n, nc, C, ldc, scr, kpk, true));
+  } else {
+    TRY(gemm<T>(st, false, n - j0, nc, b, V + j0, n, W2, b, C + j0, ldc, -1.0, 1.0, C + j0, ldc, 0.0,
+                nullptr, 0, scr, false, false, &h->launches));
+  }
+  return 0;
+}
+
+// Householder QR with explicit thin Q in the compact WY form (the fallback of Algorithm 3):
+// panels of b columns are factored with the level-2 kernels restricted to the panel, and
+// the trailing columns, then the explicit Q (accumulated backwards from [I; 0]), are updated
+// by the panel's I - V T V^H as block products, on the emulated-FP64 tensor-core engine when
+// oz is given.  Vh: n x l (ld n) for the reflectors; Wb: >= b*l elements; Rb: >= 2*b*l +
+// 2*b*b elements (W2, the panels' T factors, the panel Gram).  Narrow blocks (l < 96) take
+// the unblocked form.
+template <class T>
+int householder_blocked(chase_ctx* h, int n, int l, T* X, int ldx, T* Vh, T* Wb, T* Rb, Scratch scr,
+                        OzProd* oz) {
+  cudaStream_t st = h->stream;
+  if (l < 96) return householder_qr<T>(st, n, l, X, ldx, Vh, n, nullptr, &h->launches);
+  const int nb = l >= 192 ? 64 : 32;
+  const int np = ceil_div(l, nb);
+  T* W = Wb;
+  T* W2 = Rb;
+  T* Ts = Rb + (size_t)nb * l;
+  T* Gp = Ts + (size_t)np * nb * nb;
+  for (int k = 0; k < np; ++k) {
+    const int j0 = k * nb, b = std::min(nb, l - j0);
+    T* V = Vh + (size_t)j0 * n;
+    T* Tk = Ts + (size_t)k * nb * nb;
+    const int pc = hh_panel_coop<T>(st, n, j0, b, X, ldx, Vh, n, Gp, nb, scr, h->dstat, &h->launches);
+    if (pc == CHASE_ERR_UNSUPPORTED) {
+      TRY(hh_panel<T>(st, n, j0, b, X, ldx, Vh, n, &h->launches));
+      TRY(gemm<T>(st, true, b, b, n - j0, V + j0, n, V + j0, n, Gp, nb, 1.0, 0.0, nullptr, 0, 0.0,
+                  nullptr, 0, scr, true, false, &h->launches));
+    } else {
+      TRY(pc);
+    }
+    TRY(hh_build_T<T>(st, b, Gp, nb, Tk, nb, &h->launches));
+    TRY(wy_apply<T>(h, n, j0, b, V, Tk, nb, true, X + (size_t)(j0 + b) * ldx, ldx, l - j0 - b, W, W2,
+                    scr, oz));
+  }
+  TRY(hh_thin_identity<T>(st, n, l, X, ldx, &h->launches));
+  for (int k = np - 1; k >= 0; --k) {
+    const int j0 = k * nb, b = std::min(nb, l - j0);
+    TRY(wy_apply<T>(h, n, j0, b, Vh + (size_t)j0 * n, Ts + (size_t)k * nb * nb, nb, false,
+                    X + (size_t)j0 * ldx, ldx, l - j0, W, W2, scr, oz));
+  }
+  // a bounded wait of a panel kernel that ran out is reported, not left in the result
+  CHASE_CUDA_TRY(cudaMemcpyAsync(h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CHASE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h->hstat->timeout) return CHASE_ERR_TIMEOUT;
+  return 0;
+}
+
 // Algorithm 3 with escalation.  X (n x l, ld ldx) in place.  Workspace: Xtmp, Xsave (n x l, ld n),
 // G, Ri (l x l).  variant in/out: requested (0 = by log_est) -> used.
 template <class T>
@@ -650,7 +743,7 @@ int qr_dynamic(chase_ctx* h, int n, int l, T* X, int ldx, double log_est, double
       for (int p = 0; p < 2 && rc == 0; ++p)
         rc = cholqr_pass<T>(h, n, l, X, ldx, Xtmp, G, Ri, 0.0, scr, &info, oz);
     } else {
-      TRY(householder_qr<T>(st, n, l, X, ldx, Xtmp, n, nullptr, &h->launches));
+      TRY(householder_blocked<T>(h, n, l, X, ldx, Xtmp, G, Ri, scr, oz));
       break;
     }
     if (rc == 0) break;

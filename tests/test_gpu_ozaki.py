@@ -106,6 +106,9 @@ def test_filter_matches_oracle_fp64_tolerance(cl, handle, complex_):
     got = cl.chase_filter(handle, dev(A), dev(V), degs, c, e, l1, prec=cl.CHASE_FP64_EMU).cpu().numpy()
     err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
     assert err.max() <= 1e-11, err.max()
+    # entrywise: every entry within 1e-11 of its column's largest entry
+    ent = (np.abs(got - ref) / np.abs(ref).max(axis=0)).max()
+    assert ent <= 1e-11, ent
 
 
 @pytest.mark.parametrize("prec_name", ["CHASE_FP64_EMU", "CHASE_BF16X3"])
@@ -195,6 +198,24 @@ def test_qr_with_emulated_products_matches_oracle(cl, handle, complex_, n, l, fo
     assert orth <= (1e-10 if force == 1 else 1e-12)
     if 10.0 ** log10k <= 1e4:
         assert np.abs(Q - Qo).max() <= 1e-9
+    R = Q.conj().T @ X
+    assert np.linalg.norm(np.tril(R, -1)) <= 1e-10 * np.linalg.norm(X)
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+@pytest.mark.parametrize("n,l", [(900, 100), (1300, 200)])
+def test_householder_blocked_emulated_matches_oracle(cl, handle, complex_, n, l):
+    """The compact-WY Householder QR with its block products on the emulated-FP64 engine:
+    the oracle's Householder Q up to unit phases, orthonormal to 1e-12, R upper."""
+    X = _sv_matrix(n, l, np.logspace(0, -12, l), 700 + l, complex_)
+    Qo, vo, io = oracle.qr_dynamic(X, 0.0, force=4)
+    Xd = dev(X)
+    rc, v, info = cl.chase_qr(handle, Xd, 1.0, qr_force=4, prec=cl.CHASE_FP64_EMU)
+    Q = Xd.cpu().numpy()
+    assert rc == 0 and v == 4 and info == 0
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(l)) <= 1e-12
+    ph = np.sum(Qo.conj() * Q, axis=0)
+    np.testing.assert_allclose(np.abs(ph), 1.0, atol=1e-9)
     R = Q.conj().T @ X
     assert np.linalg.norm(np.tril(R, -1)) <= 1e-10 * np.linalg.norm(X)
 
