@@ -64,13 +64,16 @@ template <class T> __device__ inline T rot_s(const Rot& r);
 template <> __device__ inline double rot_s<double>(const Rot& r) { return r.sx; }
 template <> __device__ inline z64 rot_s<z64>(const Rot& r) { return z64{r.sx, r.sy}; }
 
-// Rotation annihilating g = H_pq from the entries H_pp, H_qq, H_pq of the current H.
+// Rotation annihilating g = H_pq from the entries H_pp, H_qq, H_pq of the current H; the
+// identity (c = 1, s = 0 exactly) when |g|^2 <= thr2 (threshold Jacobi: an entry of at most
+// u ||H||_F left in place keeps the off-diagonal norm within the stopping level l u ||H||_F).
 template <class T>
-__device__ inline Rot rot_from(int p, int q, double hpp, double hqq, T g) {
+__device__ inline Rot rot_from(int p, int q, double hpp, double hqq, T g, double thr2) {
   Rot r;
   r.p = p; r.q = q; r.c = 1.0; r.sx = 0.0; r.sy = 0.0;
-  double ag = sqrt(Sc<T>::abs2(g));
-  if (ag > 0.0) {
+  const double ag2 = Sc<T>::abs2(g);
+  double ag = sqrt(ag2);
+  if (ag > 0.0 && ag2 > thr2) {
     double tau = (hqq - hpp) / (2.0 * ag);
     double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
     double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
@@ -85,6 +88,8 @@ __device__ inline Rot rot_from(int p, int q, double hpp, double hqq, T g) {
   }
   return r;
 }
+
+__device__ inline bool rot_identity(const Rot& r) { return r.c == 1.0 && r.sx == 0.0 && r.sy == 0.0; }
 
 __device__ inline Rot load_rot(const Rot* r) {  // two 16-byte loads through L2
   const int4 a = __ldcg((const int4*)r);
@@ -111,6 +116,10 @@ __device__ inline void block_update(int l, const Rot& ra, const Rot& rb, const T
   T h_qp = va ? ldcg(Hc + (size_t)qa + (size_t)pb * ldc) : Sc<T>::zero();
   T h_pq = vb ? ldcg(Hc + (size_t)pa + (size_t)qb * ldc) : Sc<T>::zero();
   T h_qq = (va && vb) ? ldcg(Hc + (size_t)qa + (size_t)qb * ldc) : Sc<T>::zero();
+  if (rot_identity(ra) && rot_identity(rb)) {  // both rotations skipped: the block is unchanged
+    o[0] = h_pp; o[1] = h_qp; o[2] = h_pq; o[3] = h_qq;
+    return;
+  }
   // right: [col p, col q] J_b = [c col_p - conj(s) col_q, s col_p + c col_q]
   const double cb = rb.c;
   const T sb = rot_s<T>(rb), sbc = Sc<T>::conj(sb);
@@ -186,7 +195,7 @@ __device__ inline void apply_item(long long t, int l, int np, const Rot* __restr
     const long long u = t - nblk;
     const int i = (int)(u % l), b = (int)(u / l);
     const Rot rb = load_rot(rots + b);
-    if (rb.q >= l) return;
+    if (rb.q >= l || rot_identity(rb)) return;
     const double cb = rb.c;
     const T sb = rot_s<T>(rb), sbc = Sc<T>::conj(sb);
     T* wp = W + (size_t)i + (size_t)rb.p * ldw;
@@ -217,6 +226,7 @@ __global__ void __launch_bounds__(256) jacobi_sweeps_kernel(int l, int L, T* H0,
   unsigned k = 0;   // barriers passed
   int cur = 0;      // buffer holding the current H
   int sw = 0;
+  double thr2 = 0.0;  // rotation threshold^2 (none before ||H||_F is known)
   for (; sw <= max_sweeps; ++sw) {
     T* Hc = cur ? H1 : H0;
     const int ldc = cur ? ld1 : ld0;
@@ -252,13 +262,15 @@ __global__ void __launch_bounds__(256) jacobi_sweeps_kernel(int l, int L, T* H0,
       if (q < l)
         rr = rot_from<T>(p, q, Sc<T>::re(ldcg(Hc + (size_t)p + (size_t)p * ldc)),
                          Sc<T>::re(ldcg(Hc + (size_t)q + (size_t)q * ldc)),
-                         ldcg(Hc + (size_t)p + (size_t)q * ldc));
+                         ldcg(Hc + (size_t)p + (size_t)q * ldc), thr2);
       rots[i] = rr;
     }
     if (!grid_barrier(gb, G, k)) return;
     double so = 0.0, sa = 0.0;
     for (unsigned b = 0; b < G; ++b) { so += __ldcg(partial + 2 * b); sa += __ldcg(partial + 2 * b + 1); }
     if (so <= tolr * tolr * sa || so == 0.0 || sw == max_sweeps) break;
+    // the next sweep's threshold: |g| <= u ||H||_F (||H||_F does not change under rotations)
+    thr2 = 1.2325951644078309e-32 * sa;
     for (int r = 0; r < L - 1; ++r) {
       const T* Hcr = cur ? H1 : H0;
       T* Hn = cur ? H0 : H1;
@@ -276,7 +288,7 @@ __global__ void __launch_bounds__(256) jacobi_sweeps_kernel(int l, int L, T* H0,
           if (q < l)
             rr = rot_from<T>(p, q, Sc<T>::re(next_entry<T>(l, L, r, rc, Hcr, ldcr, p, p)),
                              Sc<T>::re(next_entry<T>(l, L, r, rc, Hcr, ldcr, q, q)),
-                             next_entry<T>(l, L, r, rc, Hcr, ldcr, p, q));
+                             next_entry<T>(l, L, r, rc, Hcr, ldcr, p, q), thr2);
           rn[i] = rr;
         }
       }
