@@ -150,20 +150,31 @@ __device__ inline int pair_index(int L, int round, int x) {
   return d <= (m - 1) / 2 ? d : m - d;
 }
 
-// Entry (x, y) of the next H (x != y or x == y), formed from the current H and the
-// round's rotations exactly as the owner of its block forms it.
+// The next round's rotation for pair (p, q), from the entries (p, p), (q, q), (p, q) of the
+// next H formed exactly as their blocks' owners form them: both rotations are loaded once,
+// then the three 2x2 blocks' loads are independent of one another (two dependent L2 round
+// trips in all, not six).
 template <class T>
-__device__ inline T next_entry(int l, int L, int round, const Rot* rots, const T* Hc, int ldc, int x,
-                               int y) {
-  const int ax = pair_index(L, round, x), ay = pair_index(L, round, y);
-  const int a = ax < ay ? ax : ay, b = ax < ay ? ay : ax;
-  const Rot ra = load_rot(rots + a), rb = load_rot(rots + b);
-  T o[4];
-  block_update<T>(l, ra, rb, Hc, ldc, o);
-  // block (a, b) holds rows {ra.p, ra.q} x columns {rb.p, rb.q}; (x, y) or its mirror
-  const int r = ax <= ay ? x : y, c = ax <= ay ? y : x;
-  const T v = (r == ra.p) ? (c == rb.p ? o[0] : o[2]) : (c == rb.p ? o[1] : o[3]);
-  return ax <= ay ? v : Sc<T>::conj(v);
+__device__ inline Rot next_rotation(int l, int L, int round, const Rot* rots, const T* Hc, int ldc,
+                                    int p, int q, double thr2) {
+  const int ap = pair_index(L, round, p), aq = pair_index(L, round, q);
+  const Rot rp = load_rot(rots + ap), rq = load_rot(rots + aq);
+  T opp[4], oqq[4], opq[4];
+  block_update<T>(l, rp, rp, Hc, ldc, opp);
+  block_update<T>(l, rq, rq, Hc, ldc, oqq);
+  if (ap <= aq) block_update<T>(l, rp, rq, Hc, ldc, opq);
+  else block_update<T>(l, rq, rp, Hc, ldc, opq);
+  const double hpp = Sc<T>::re(p == rp.p ? opp[0] : opp[3]);
+  const double hqq = Sc<T>::re(q == rq.p ? oqq[0] : oqq[3]);
+  // block (a, b) holds rows {ra.p, ra.q} x columns {rb.p, rb.q}; (p, q) or its mirror
+  T g;
+  if (ap <= aq) {
+    g = (p == rp.p) ? (q == rq.p ? opq[0] : opq[2]) : (q == rq.p ? opq[1] : opq[3]);
+  } else {
+    const T v = (q == rq.p) ? (p == rp.p ? opq[0] : opq[2]) : (p == rp.p ? opq[1] : opq[3]);
+    g = Sc<T>::conj(v);
+  }
+  return rot_from<T>(p, q, hpp, hqq, g, thr2);
 }
 
 // Work item t of a round's update, from the current H (Hc) into the next (Hn): t < np^2
@@ -285,10 +296,7 @@ __global__ void __launch_bounds__(256) jacobi_sweeps_kernel(int l, int L, T* H0,
           pair_of(L, r + 1, i, p, q);
           Rot rr;
           rr.p = p; rr.q = q; rr.c = 1.0; rr.sx = 0.0; rr.sy = 0.0;
-          if (q < l)
-            rr = rot_from<T>(p, q, Sc<T>::re(next_entry<T>(l, L, r, rc, Hcr, ldcr, p, p)),
-                             Sc<T>::re(next_entry<T>(l, L, r, rc, Hcr, ldcr, q, q)),
-                             next_entry<T>(l, L, r, rc, Hcr, ldcr, p, q), thr2);
+          if (q < l) rr = next_rotation<T>(l, L, r, rc, Hcr, ldcr, p, q, thr2);
           rn[i] = rr;
         }
       }
