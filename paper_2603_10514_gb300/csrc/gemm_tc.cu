@@ -13,16 +13,16 @@
 // multiple of 64 elements, zero padded); V planes column-major with K
 // contiguous (same kp); FP64 blocks column-major with leading dimension ldv.
 //
-// One CTA computes one 128 x 128 output tile; 256 threads in four roles:
-//   warp 0      TMA producer: 4 tiles (Ah, Al, Vh, Vl; 64 x 128 BF16 each,
-//               128-byte swizzle) per 64-wide K block into a 3-stage ring;
-//   warp 1      allocates 128 TMEM columns; one thread issues
-//               tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16),
-//               12 per K block, and commits each stage back to the producer;
-//   warps 4..7  epilogue: tcgen05.ld of its 32 TMEM lanes (tile rows), FP64
-//               three-term update, BF16 split of the result.
-// Every mbarrier wait is bounded (~2 s of clock64); on expiry the kernel sets
-// a flag in the device status word, drains, frees its TMEM and returns.
+// CTA pairs (clusters of two along grid x), one pair per 256-row block and column tile of
+// BN <= 256: the even CTA issues tcgen05.mma.cta_group::2.kind::f16 (M 256, N BN, K 16),
+// three per K step (Ah Vh, Ah Vl, Al Vh) into one FP32 accumulator in TMEM (its 128 rows in
+// each CTA); each CTA loads its own 128 rows of Ah and Al and half of the tile's rows of Vh
+// and Vl (TMA, 128-byte swizzle, 64-wide K blocks, three 64 KB stages: 12 MMAs per barrier
+// round trip); 16 epilogue warps per CTA read TMEM (tcgen05.ld), apply the FP64 three-term
+// update and write the BF16 split of the result.  Same structure as the modular-product
+// kernel of gemm_oz.cu (and its measured reasons).
+// Every mbarrier wait is bounded (~2 s of clock64); on expiry the kernel sets a flag in the
+// device status word, drains, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -31,217 +31,140 @@
 #include "../../include/chase_gb300.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "tcgen05.cuh"
 
 namespace chase {
 
 namespace {
 
-constexpr int TBM = 128;
-constexpr int TBN = 128;
-constexpr int TBK = 64;  // 64 BF16 = one 128-byte swizzle row
+using namespace tc;
+
+constexpr int TBM = 128;   // rows of A per CTA (a pair covers 256)
+constexpr int TBK = 64;    // 64 BF16 = one 128-byte swizzle row
+constexpr int TBN_MAX = 256;
 constexpr int TSTAGES = 3;
-constexpr int TILE_BYTES = TBM * TBK * 2;            // 16 KB per operand tile
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // Ah, Al, Vh, Vl
-constexpr int TC_THREADS = 256;
+constexpr int T_A1 = TBM * TBK * 2;                 // 16 KB: 128 rows of Ah (or Al)
+constexpr int T_B1 = (TBN_MAX / 2) * TBK * 2;       // 16 KB: up to 128 rows of Vh (or Vl)
+constexpr int STAGE_BYTES = 2 * T_A1 + 2 * T_B1;    // Ah, Al, Vh half, Vl half
+constexpr int TC_EPI_WARPS = 16;
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr int TC_SMEM = TSTAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: returns false if the phase did not complete within kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand tile whose rows are 128 bytes,
-// 128-byte swizzle, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;               // LBO (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;     // SBO
-  d |= (uint64_t)1 << 46;               // version
-  d |= (uint64_t)2 << 61;               // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
+constexpr uint32_t TC_TMEM_COLS = TBN_MAX;
+static_assert(TC_SMEM <= 232448, "shared memory");
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_filter_bf16x3_kernel(const __grid_constant__ CUtensorMap mapAh,
                             const __grid_constant__ CUtensorMap mapAl,
                             const __grid_constant__ CUtensorMap mapVh,
-                            const __grid_constant__ CUtensorMap mapVl, int M, int N, int nkb,
-                            int col0, double alpha, double beta, const double* X64, double gamma,
-                            const double* Z64, double* out64, int ldv, __nv_bfloat16* next_h,
-                            __nv_bfloat16* next_l, int kp, DevStatus* status) {
+                            const __grid_constant__ CUtensorMap mapVl, int M, int N, int BN,
+                            int ntile, int nkb, int col0, double alpha, double beta,
+                            const double* X64, double gamma, const double* Z64, double* out64,
+                            int ldv, __nv_bfloat16* next_h, __nv_bfloat16* next_l, int kp,
+                            DevStatus* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + TSTAGES * STAGE_BYTES);
-  uint64_t* empty = full + TSTAGES;
-  uint64_t* tmem_full = empty + TSTAGES;
-  uint32_t* tmem_slot = (uint32_t*)(tmem_full + 1);
-  int* s_err = (int*)(tmem_slot + 1);
+  uint64_t* full = (uint64_t*)(smem + TSTAGES * STAGE_BYTES);  // [TSTAGES] (the even CTA's)
+  uint64_t* empty = full + TSTAGES;                            // [TSTAGES]
+  uint64_t* tfull = empty + TSTAGES;                           // accumulator complete
+  uint32_t* tslot = (uint32_t*)(tfull + 1);
+  int* s_err = (int*)(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * TBN, m0 = blockIdx.y * TBM;
+  const uint32_t rank = cluster_rank();
+  // pair index p = blockIdx.x / 2 over (row pair, column tile), column tiles fastest
+  const int pr = (int)(blockIdx.x >> 1);
+  const int n0 = (pr % ntile) * BN, m0 = (2 * (pr / ntile) + (int)(blockIdx.x & 1)) * TBM;
+  const int half = BN >> 1;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TSTAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(tmem_full, 1);
+    for (int i = 0; i < TSTAGES; ++i) { bar_init(&full[i], 1); bar_init(&empty[i], 1); }
+    bar_init(tfull, 1);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(TBN));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  if (warp == 1) {  // one warp of each CTA of the pair allocates the pair's accumulator
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s32(tslot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  cluster_sync();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = *tslot;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    for (int kb = 0; kb < nkb; ++kb) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    const uint32_t bytes = (uint32_t)(2 * (2 * T_A1) + 2 * BN * TBK * 2);  // the pair's copies
+    const uint32_t full0 = peer_addr(full, 0);
+    int issued = 0;
+    for (int kb = 0; kb < nkb && !*(volatile int*)s_err; ++kb) {
       const int s = kb % TSTAGES;
-      const uint32_t ph = (uint32_t)((kb / TSTAGES) & 1);
-      if (!mbar_wait(&empty[s], ph ^ 1)) { atomicOr(s_err, 1); break; }
-      if (*(volatile int*)s_err) break;
+      if (!bar_wait(&empty[s], (uint32_t)(((kb / TSTAGES) & 1) ^ 1))) { atomicOr(s_err, 1); break; }
+      if (rank == 0) bar_expect(&full[s], bytes);
       unsigned char* st = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      const int k = kb * TBK;
-      tma_load_2d(st + 0 * TILE_BYTES, &mapAh, &full[s], k, m0);
-      tma_load_2d(st + 1 * TILE_BYTES, &mapAl, &full[s], k, m0);
-      tma_load_2d(st + 2 * TILE_BYTES, &mapVh, &full[s], k, col0 + n0);
-      tma_load_2d(st + 3 * TILE_BYTES, &mapVl, &full[s], k, col0 + n0);
+      const uint32_t fb = full0 + 8u * (uint32_t)s;
+      const int k = kb * TBK, vrow = col0 + n0 + (int)rank * half;
+      tma2_pair(st, &mapAh, fb, k, m0);
+      tma2_pair(st + T_A1, &mapAl, fb, k, m0);
+      tma2_pair(st + 2 * T_A1, &mapVh, fb, k, vrow);
+      tma2_pair(st + 2 * T_A1 + T_B1, &mapVl, fb, k, vrow);
+      issued = kb + 1;
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    constexpr uint32_t idesc = idesc_bf16(TBM, TBN);
+    for (int kb = issued; kb < issued + TSTAGES; ++kb)
+      if (!bar_wait(&empty[kb % TSTAGES], (uint32_t)(((kb / TSTAGES) & 1) ^ 1))) { atomicOr(s_err, 1); break; }
+    if (rank == 0)
+      for (int b = max(0, issued - TSTAGES); b < issued; ++b)
+        if (!bar_wait(&full[b % TSTAGES], (uint32_t)((b / TSTAGES) & 1))) { atomicOr(s_err, 1); break; }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---------------- MMA issuer (even CTA): M 256 x N BN x K 16, three per K step ----------------
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)((2 * TBM) >> 4) << 24);
+    bool bad = false;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % TSTAGES;
-      const uint32_t ph = (uint32_t)((kb / TSTAGES) & 1);
-      if (!mbar_wait(&full[s], ph)) { atomicOr(s_err, 2); break; }
+      if (!bar_poll(&full[s], (uint32_t)((kb / TSTAGES) & 1))) { bad = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-      const uint64_t dAh = smem_desc_sw128(base + 0 * TILE_BYTES);
-      const uint64_t dAl = smem_desc_sw128(base + 1 * TILE_BYTES);
-      const uint64_t dVh = smem_desc_sw128(base + 2 * TILE_BYTES);
-      const uint64_t dVl = smem_desc_sw128(base + 3 * TILE_BYTES);
+      const uint32_t sa = s32(smem + s * STAGE_BYTES);
+      const uint64_t dAh = desc_sw128(sa), dAl = desc_sw128(sa + T_A1);
+      const uint64_t dVh = desc_sw128(sa + 2 * T_A1), dVl = desc_sw128(sa + 2 * T_A1 + T_B1);
 #pragma unroll
       for (int kk = 0; kk < TBK / 16; ++kk) {
-        const uint64_t off = (uint64_t)((kk * 16 * 2) >> 4);  // 32 bytes per K=16 step
-        mma_bf16(tmem, dAh + off, dVh + off, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-        mma_bf16(tmem, dAh + off, dVl + off, idesc, 1u);
-        mma_bf16(tmem, dAl + off, dVh + off, idesc, 1u);
+        const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes per K = 16 step
+        mma_pair(tmem, dAh + off, dVh + off, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_pair(tmem, dAh + off, dVl + off, idesc, 1u);
+        mma_pair(tmem, dAl + off, dVh + off, idesc, 1u);
       }
-      mma_commit(&empty[s]);
+      commit_pair(&empty[s]);
     }
-    mma_commit(tmem_full);
-  } else if (warp >= 4) {
-    // ---------------- epilogue ----------------
-    const int q = warp - 4;  // TMEM lanes 32q .. 32q+31 = tile rows
-    bool ok = mbar_wait(tmem_full, 0);
-    if (!ok) atomicOr(s_err, 4);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (bad) atomicOr(s_err, 2);
+    commit_pair(tfull);
+  } else if (warp >= 2) {
+    // ---------------- epilogue (both CTAs: own TMEM lanes = own 128 rows) ----------------
+    const int q = warp & 3, cq = (warp - 2) >> 2;  // lane quarter, column quarter
     const int r = m0 + 32 * q + lane;
+    const int cw = BN >> 2;
+    const bool ok = __all_sync(0xffffffffu, bar_wait(tfull, 0u));
+    if (!ok && lane == 0) atomicOr(s_err, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok && !*(volatile int*)s_err) {
-      for (int cb = 0; cb < TBN / 32; ++cb) {
-        float acc[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cb * 32), acc);
+      for (int cb = 0; cb * 32 < cw; ++cb) {
+        uint32_t v[32];
+        ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cq * cw + cb * 32), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (r < M) {
-#pragma unroll 4
+#pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int c = n0 + cb * 32 + j;
-            if (c >= N) break;
+            const int jj = cb * 32 + j;
+            const int c = n0 + cq * cw + jj;
+            if (jj >= cw || c >= N) continue;
             const size_t idx = (size_t)r + (size_t)(col0 + c) * ldv;
-            double v = alpha * (double)acc[j];
-            if (beta != 0.0) v = fma(beta, X64[idx], v);
-            if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
-            out64[idx] = v;
-            const __nv_bfloat16 hi = __double2bfloat16(v);
-            const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+            double y = alpha * (double)__uint_as_float(v[j]);
+            if (beta != 0.0) y = fma(beta, X64[idx], y);
+            if (gamma != 0.0) y = fma(gamma, Z64[idx], y);
+            out64[idx] = y;
+            const __nv_bfloat16 hi = __double2bfloat16(y);
+            const __nv_bfloat16 lo = __double2bfloat16(y - (double)__bfloat162float(hi));
             const size_t bidx = (size_t)r + (size_t)(col0 + c) * kp;
             next_h[bidx] = hi;
             next_l[bidx] = lo;
@@ -252,11 +175,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (warp == 1 && !bar_wait(tfull, 0u) && lane == 0) atomicOr(s_err, 8);
+  cluster_sync();  // neither CTA frees the pair's TMEM or exits while the other may signal it
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
   }
-  if (threadIdx.x == 0 && *s_err) atomicOr(&status->timeout, *s_err);
+  if (threadIdx.x == 32 && *s_err) atomicOr(&status->timeout, *s_err);
 }
 
 // ---------------- operand preparation ----------------
@@ -350,13 +275,13 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // 2-D BF16 tensor map: inner dimension `inner` (contiguous, row length kp elements),
-// `outer` rows; box 64 x 128 with 128-byte swizzle.
-int make_map(CUtensorMap* map, const void* base, int kp, int outer) {
+// `outer` rows; box 64 x box_rows with 128-byte swizzle.
+int make_map(CUtensorMap* map, const void* base, int kp, int outer, int box_rows) {
   auto enc = get_encode();
   if (!enc) return CHASE_ERR_CUDA;
   cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)outer};
   cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-  cuuint32_t box[2] = {TBK, 128};
+  cuuint32_t box[2] = {TBK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -410,18 +335,33 @@ int tc_filter_step(cudaStream_t st, int M, int kp, const void* Ah, const void* A
                    double* out64, int ldv, void* Vh_out, void* Vl_out, DevStatus* dst,
                    int* launches) {
   if (N <= 0) return 0;
+  // column tiles of at most 256 (a multiple of 16), as even as possible; CTA pairs over
+  // 256-row blocks
+  const int ntile = ceil_div(N, TBN_MAX);
+  const int BN = ceil_div(ceil_div(N, ntile), 16) * 16;
   CUtensorMap mAh, mAl, mVh, mVl;
-  if (make_map(&mAh, Ah, kp, M) || make_map(&mAl, Al, kp, M) ||
-      make_map(&mVh, Vh_in, kp, ncols_total) || make_map(&mVl, Vl_in, kp, ncols_total))
+  if (make_map(&mAh, Ah, kp, M, TBM) || make_map(&mAl, Al, kp, M, TBM) ||
+      make_map(&mVh, Vh_in, kp, ncols_total, BN / 2) || make_map(&mVl, Vl_in, kp, ncols_total, BN / 2))
     return CHASE_ERR_CUDA;
   CHASE_CUDA_TRY(cudaFuncSetAttribute(tc_filter_bf16x3_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-  dim3 grid(ceil_div(N, TBN), ceil_div(M, TBM));
-  tc_filter_bf16x3_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(
-      mAh, mAl, mVh, mVl, M, N, kp / TBK, col0, alpha, beta, X64, gamma, Z64, out64, ldv,
-      (__nv_bfloat16*)Vh_out, (__nv_bfloat16*)Vl_out, kp, dst);
+  const int mblk = ceil_div(M, 2 * TBM) * 2;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ntile * mblk);
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = TC_SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  CHASE_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_filter_bf16x3_kernel, mAh, mAl, mVh, mVl, M, N, BN, ntile,
+                                    kp / TBK, col0, alpha, beta, X64, gamma, Z64, out64, ldv,
+                                    (__nv_bfloat16*)Vh_out, (__nv_bfloat16*)Vl_out, kp, dst));
   if (launches) ++*launches;
-  CHASE_CUDA_TRY(cudaGetLastError());
   return 0;
 }
 
