@@ -388,16 +388,14 @@ __global__ void __launch_bounds__(M_THREADS, 1)
 // R holds `splits` partial residues per modulus; they are summed mod p_j first.
 // ---------------------------------------------------------------------------
 // Returns the FP64 rounding m of |X| and the sign, with X = m 2^{*shift}.
-__device__ __forceinline__ double crt_value(const uint8_t* __restrict__ R, size_t stride_z,
-                                            size_t idx, int splits, int* shift_out) {
+// X = sum_j r_j C_j mod P from the residues r_j < p_j, rounded once to FP64: returns the
+// signed magnitude and *shift_out with |X| = |value| 2^shift.
+__device__ __forceinline__ double crt_combine(const uint32_t* rj, int* shift_out) {
   unsigned long long acc[5] = {0, 0, 0, 0, 0};
 #pragma unroll
   for (int j = 0; j < kOzModuli; ++j) {
-    uint32_t rj = R[(size_t)j * stride_z + idx];
-    for (int s = 1; s < splits; ++s) rj += R[(size_t)(s * kOzModuli + j) * stride_z + idx];
-    rj %= (uint32_t)oz_modulus(j);
 #pragma unroll
-    for (int l = 0; l < 5; ++l) acc[l] += (unsigned long long)rj * c_crt.C[j][l];
+    for (int l = 0; l < 5; ++l) acc[l] += (unsigned long long)rj[j] * c_crt.C[j][l];
   }
   uint32_t x[5];
   unsigned long long carry = 0;
@@ -486,6 +484,35 @@ __device__ __forceinline__ double crt_value(const uint8_t* __restrict__ R, size_
   return neg ? -mag : mag;
 }
 
+__device__ __forceinline__ double crt_value(const uint8_t* __restrict__ R, size_t stride_z,
+                                            size_t idx, int splits, int* shift_out) {
+  uint32_t rj[kOzModuli];
+#pragma unroll
+  for (int j = 0; j < kOzModuli; ++j) {
+    uint32_t r = R[(size_t)j * stride_z + idx];
+    for (int s = 1; s < splits; ++s) r += R[(size_t)(s * kOzModuli + j) * stride_z + idx];
+    rj[j] = r % (uint32_t)oz_modulus(j);
+  }
+  return crt_combine(rj, shift_out);
+}
+
+// The epilogue of one reconstructed entry: v = alpha 2^E x + beta X64 + gamma Z64.
+__device__ __forceinline__ void crt_store(double x, int sh, int r, int c, const int* __restrict__ rowexp,
+                                          const int* __restrict__ colexp, int col0, double alpha,
+                                          double beta, const double* X64, double gamma,
+                                          const double* Z64, double* out64, int ldo) {
+  // x 2^E with |x| in [2^63, 2^64]: one exact multiply by the power of two 2^E built from
+  // its exponent field when that is a normal number (ldexp otherwise)
+  const int E = sh + rowexp[r] + colexp[col0 + c] - 2 * OZ_KBITS;
+  const double v0 = (E > -1022 && E < 1024) ? x * __longlong_as_double((long long)(E + 1023) << 52)
+                                            : ldexp(x, E);
+  const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
+  double v = alpha * v0;
+  if (beta != 0.0) v = fma(beta, X64[idx], v);
+  if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
+  out64[idx] = v;
+}
+
 __global__ void __launch_bounds__(256) crt_kernel(int M, int N, int splits, const uint8_t* __restrict__ R,
                                                   const int* __restrict__ rowexp,
                                                   const int* __restrict__ colexp, int col0,
@@ -499,16 +526,41 @@ __global__ void __launch_bounds__(256) crt_kernel(int M, int N, int splits, cons
     const int r = (int)(t % M), c = (int)(t / M);
     int sh;
     const double x = crt_value(R, stride_z, t, splits, &sh);
-    // x 2^E with |x| in [2^63, 2^64]: one exact multiply by the power of two 2^E built from
-    // its exponent field when that is a normal number (ldexp otherwise)
-    const int E = sh + rowexp[r] + colexp[col0 + c] - 2 * OZ_KBITS;
-    const double v0 = (E > -1022 && E < 1024) ? x * __longlong_as_double((long long)(E + 1023) << 52)
-                                              : ldexp(x, E);
-    const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
-    double v = alpha * v0;
-    if (beta != 0.0) v = fma(beta, X64[idx], v);
-    if (gamma != 0.0) v = fma(gamma, Z64[idx], v);
-    out64[idx] = v;
+    crt_store(x, sh, r, c, rowexp, colexp, col0, alpha, beta, X64, gamma, Z64, out64, ldo);
+  }
+}
+
+// crt_kernel for M N divisible by 4: four consecutive entries per thread, each residue plane
+// read as one 4-byte word (a warp reads 128 contiguous bytes per plane instead of 32).
+__global__ void __launch_bounds__(256) crt4_kernel(int M, int N, int splits, const uint8_t* __restrict__ R,
+                                                   const int* __restrict__ rowexp,
+                                                   const int* __restrict__ colexp, int col0,
+                                                   double alpha, double beta, const double* X64,
+                                                   double gamma, const double* Z64, double* out64,
+                                                   int ldo) {
+  const size_t total = (size_t)M * N, quads = total / 4;
+  const uint32_t* R4 = (const uint32_t*)R;
+  const size_t stride4 = total / 4;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < quads;
+       q += (size_t)gridDim.x * blockDim.x) {
+    uint32_t w[kOzModuli], w2[kOzModuli];
+#pragma unroll
+    for (int j = 0; j < kOzModuli; ++j) {
+      w[j] = __ldg(R4 + (size_t)j * stride4 + q);
+      w2[j] = splits > 1 ? __ldg(R4 + (size_t)(kOzModuli + j) * stride4 + q) : 0u;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t rj[kOzModuli];
+#pragma unroll
+      for (int j = 0; j < kOzModuli; ++j)
+        rj[j] = (((w[j] >> (8 * e)) & 0xFFu) + ((w2[j] >> (8 * e)) & 0xFFu)) % (uint32_t)oz_modulus(j);
+      int sh;
+      const double x = crt_combine(rj, &sh);
+      const size_t t = 4 * q + e;
+      crt_store(x, sh, (int)(t % M), (int)(t / M), rowexp, colexp, col0, alpha, beta, X64, gamma, Z64,
+                out64, ldo);
+    }
   }
 }
 
@@ -949,8 +1001,14 @@ int crt_launch(cudaStream_t st, int M, int N, int S, Scratch resbuf, const int* 
                double gamma, const double* Z64, double* out64, int ldo, int* launches) {
   const size_t total = (size_t)M * N;
   const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16));
-  crt_kernel<<<blocks, 256, 0, st>>>(M, N, S, (const uint8_t*)resbuf.ptr, rowexp, colexp, col0, alpha,
-                                     beta, X64, gamma, Z64, out64, ldo);
+  if (total % 4 == 0) {
+    const int b4 = (int)std::max<size_t>(1, std::min<size_t>((total / 4 + 255) / 256, (size_t)kNumSMs * 16));
+    crt4_kernel<<<b4, 256, 0, st>>>(M, N, S, (const uint8_t*)resbuf.ptr, rowexp, colexp, col0, alpha, beta,
+                                    X64, gamma, Z64, out64, ldo);
+  } else {
+    crt_kernel<<<blocks, 256, 0, st>>>(M, N, S, (const uint8_t*)resbuf.ptr, rowexp, colexp, col0, alpha,
+                                       beta, X64, gamma, Z64, out64, ldo);
+  }
   if (launches) ++*launches;
   CHASE_CUDA_TRY(cudaGetLastError());
   return 0;
