@@ -642,12 +642,18 @@ __device__ __forceinline__ void write_residues(double x, int e, __nv_bfloat16* b
     else if (sh > -64) X = (m + (1LL << (-sh - 1))) >> (-sh);
     if (bits < 0) X = -X;
   }
+  // |X| < 2^58 as two 29-bit halves: |X| mod p = (U1 (2^29 mod p) + U0) mod p in 32-bit
+  // arithmetic (remainders by compile-time constants)
+  const unsigned long long U = (unsigned long long)(X < 0 ? -X : X);
+  const uint32_t U1 = (uint32_t)(U >> 29), U0 = (uint32_t)(U & ((1u << 29) - 1));
 #pragma unroll
   for (int j = 0; j < kOzModuli; ++j) {
-    const int p = oz_modulus(j);
-    int rr = (int)(X % p);  // in (-p, p), sign of X
-    if (rr > p / 2) rr -= p;
-    else if (rr < -(p / 2)) rr += p;
+    const uint32_t p = (uint32_t)oz_modulus(j);
+    const uint32_t k29 = (uint32_t)((1ull << 29) % p);
+    const uint32_t u = ((U1 % p) * k29 + U0 % p) % p;   // |X| mod p in [0, p)
+    int rr = X < 0 ? -(int)u : (int)u;                   // X mod p in (-p, p), sign of X
+    if (rr > (int)p / 2) rr -= (int)p;
+    else if (rr < -((int)p / 2)) rr += (int)p;
     base[idx + (size_t)j * plane] = __int2bfloat16_rn(rr);  // exact: |rr| <= 128
   }
 }
