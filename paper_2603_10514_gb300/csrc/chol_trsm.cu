@@ -141,10 +141,11 @@ __global__ void __launch_bounds__(1024) add_shift_kernel(int n, T* G, int ldg, d
   }
 }
 
-// Factors the b x b diagonal block at (off, off) in shared memory (upper, in place).
+// Factors the b x b diagonal block at (off, off) in shared memory (upper, in place): one CTA
+// of 1024 threads (the rank-1 updates of a 64 x 64 block take 2 entries per thread).
 template <class T>
-__global__ void __launch_bounds__(256) chol_diag_kernel(int b, T* G, int ldg, int off,
-                                                        DevStatus* dst) {
+__global__ void __launch_bounds__(1024) chol_diag_kernel(int b, T* G, int ldg, int off,
+                                                         DevStatus* dst) {
   extern __shared__ unsigned char diag_smem[];
   T(*B)[CNB + 1] = reinterpret_cast<T(*)[CNB + 1]>(diag_smem);  // CNB x (CNB + 1)
   __shared__ double s_piv;
@@ -198,13 +199,14 @@ int potrf_upper_blocked(cudaStream_t st, int n, T* G, int ldg, double shift_fact
                                       dsmem));
   for (int off = 0; off < n; off += CNB) {
     const int b = std::min(CNB, n - off);
-    chol_diag_kernel<T><<<1, 256, dsmem, st>>>(b, G, ldg, off, dst);
+    chol_diag_kernel<T><<<1, 1024, dsmem, st>>>(b, G, ldg, off, dst);
     if (launches) ++*launches;
     const int rest = n - off - b;
     if (rest <= 0) break;
     T* Gkk = G + (size_t)off + (size_t)off * ldg;
     T* Gpanel = G + (size_t)off + (size_t)(off + b) * ldg;        // b x rest
     T* Gtrail = G + (size_t)(off + b) + (size_t)(off + b) * ldg;  // rest x rest
+    // the inverse of the diagonal block: one CTA per column (its FP64 work over b SMs)
     int rc = trtri_upper<T>(st, b, Gkk, ldg, Rkk_inv, b, launches);
     if (rc) return rc;
     // block row: R_k. = R_kk^{-H} G_k.

@@ -174,7 +174,14 @@ int gemm(cudaStream_t st, bool transA, int M, int N, int K, const T* A, int lda,
          int ldb, T* C, int ldc, double alpha, double beta, const T* X, int ldx, double gamma,
          const T* Y, int ldy, Scratch scratch, bool upper_only, bool tri_b, int* launches) {
   if (M <= 0 || N <= 0) return 0;
-  const int TN = (N > 16) ? 2 : 1;
+  // 64 x 32 tiles; 64 x 16 when N <= 16, or when a short product (K <= 256, no room for
+  // split-K) would otherwise leave SMs idle: twice the CTAs, each with half the FP64 work
+  int TN = (N > 16) ? 2 : 1;
+  if (TN == 2 && K <= 256) {
+    long long t2 = (long long)ceil_div(M, BM) * ceil_div(N, 32);
+    if (upper_only) t2 = (t2 + ceil_div(M, BM)) / 2;
+    if (t2 < 2LL * kNumSMs) TN = 1;
+  }
   const int BN = 16 * TN;
   const int tm = ceil_div(M, BM), tn = ceil_div(N, BN);
   long long tiles = (long long)tm * tn;
