@@ -171,6 +171,10 @@ def _ld(t, name):
         raise ValueError("%s must be a CUDA tensor" % name)
     if t.dim() == 2 and t.numel() == 0:
         return max(1, t.shape[0])
+    if t.dim() == 2 and t.shape[1] == 1 and (t.stride(0) == 1 or t.shape[0] == 1):
+        return max(1, t.shape[0])   # one column: the column stride is never used
+    if t.dim() == 2 and t.shape[0] == 1 and t.stride(1) >= 1:
+        return t.stride(1)          # one row: the row stride is never used
     if t.dim() != 2 or t.stride(0) != 1 or t.stride(1) < max(1, t.shape[0]):
         raise ValueError("%s must be column-major (strides (1, ld)), got strides %s" % (name, t.stride()))
     return t.stride(1)

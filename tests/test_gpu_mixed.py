@@ -60,7 +60,7 @@ def stack_v(V):
 
 
 @pytest.mark.parametrize("complex_", [False, True])
-@pytest.mark.parametrize("n,ncols", [(333, 37), (1000, 300)])
+@pytest.mark.parametrize("n,ncols", [(333, 37), (1000, 300), (40, 1), (129, 257)])
 def test_one_step_matches_split_products(cl, handle, complex_, n, ncols):
     lam = W.spectrum_uniform(n, -1.0, 1.0, 3)
     A = W.known_spectrum_matrix(lam, 3, complex_).numpy()

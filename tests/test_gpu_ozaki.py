@@ -43,13 +43,19 @@ def dev(x):
 
 
 @pytest.mark.parametrize("complex_", [False, True])
-@pytest.mark.parametrize("n,ncols", [(333, 37), (517, 70), (1000, 130)])
+@pytest.mark.parametrize("n,ncols", [
+    (333, 37), (517, 70), (1000, 130),
+    (40, 1),       # one row block (the pair's odd CTA has no rows), narrowest column tile
+    (64, 16),      # K of one or two 64-wide blocks, a 16-column tile (8-row halves)
+    (129, 257),    # ragged: two column tiles, two row blocks
+])
 def test_one_step_is_fp64_accurate(cl, handle, complex_, n, ncols):
     lam = W.spectrum_uniform(n, -3.0, 40.0, 3)
     A = W.known_spectrum_matrix(lam, 3, complex_).numpy()
     V = W.start_block(n, ncols, 4, complex_)
-    V[:, 1] *= 1e-9          # columns of very different scale
-    V[5, 2] = 1e3            # one large entry
+    if ncols > 2:
+        V[:, 1] *= 1e-9      # columns of very different scale
+        V[5, 2] = 1e3        # one large entry
     c, e, l1 = 20.0, 21.0, -5.0
     got = cl.chase_filter(handle, dev(A), dev(V), [1] * ncols, c, e, l1,
                           prec=cl.CHASE_FP64_EMU).cpu().numpy()
