@@ -47,15 +47,16 @@ def _measured_peaks():
 
 
 BF16_PEAK_TFLOPS, BF16_SUSTAINED_TFLOPS = _measured_peaks()
-# BF16 tensor-core products per real FP64 product in the emulated mode: one modular product
-# per modulus of the Ozaki scheme II (17 moduli <= 256).
-OZAKI_PAIRS = 17
+# BF16 tensor-core work per FP64-equivalent flop in the emulated mode: one modular product per
+# modulus of the Ozaki scheme II (17 moduli <= 256); a complex product is three real products
+# of order n (Gauss's form: Ar Vr, Ai Vi, (Ar + Ai)(Vr + Vi)), 3 x 2 n^2 per column against the
+# 8 n^2 FP64-equivalent flops of a complex column MatVec: 17 x 3/4 = 12.75 (17 for real).
+OZAKI_MODULI = 17
+OZAKI_PAIRS = OZAKI_MODULI * 0.75   # the default workload is complex
 # DRAM bytes (read + write) of one emulated product of the default workload (complex
-# n = 10000, 600 active columns), measured by one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, 1 pass) of the CTA-pair modular-product kernel: 15.68 GB read and
-# 0.268 GB written; the CRT kernel 0.300 GB read and 0.076 GB written.  Launches with fewer
-# active columns read the same residue planes of A, which are most of it.
-OZ_TRAFFIC_PER_LAUNCH = 15.676e9 + 0.268e9 + 0.300e9 + 0.076e9
+# n = 10000, 600 active columns): none measured for the three-product form yet (the stacked
+# form's capture, 16.3 GB per product, no longer applies).
+OZ_TRAFFIC_PER_LAUNCH = None
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
@@ -148,10 +149,13 @@ def run_filter(args):
     if args.prec == "fp64":
         line["frac_of_fp64_peak"] = flops / t / 1e12 / FP64_PEAK_TFLOPS
     else:
-        # BF16 tensor-core products of the stacked real operator (2n x 2n) per step:
-        # 3 for BF16x3, OZAKI_PAIRS modular products for the Ozaki scheme II
-        npairs = 3 if args.prec == "bf16x3" else OZAKI_PAIRS
-        tc = npairs * 2.0 * (2 * n) * (2 * n) * k * args.degree / t / 1e12
+        # BF16 tensor-core work per step: BF16x3 three products of the stacked real operator
+        # (2n x 2n); the Ozaki scheme II 17 modular products of each of Gauss's three real
+        # products of order n
+        if args.prec == "bf16x3":
+            tc = 3 * 2.0 * (2 * n) * (2 * n) * k * args.degree / t / 1e12
+        else:
+            tc = OZAKI_MODULI * 3 * 2.0 * n * n * k * args.degree / t / 1e12
         line["bf16_tensor_tflops"] = tc
         line["frac_of_bf16_peak"] = tc / BF16_PEAK_TFLOPS
     print(json.dumps(line), flush=True)
@@ -710,10 +714,11 @@ def main():
         lp = st["filter_flops_lowprec"]
         tc_flops = OZAKI_PAIRS * (st["filter_flops"] - lp) + 3.0 * lp
         pipe = tc_flops / nl / dur_launch / 1e12 if dur_launch > 0 else None
-        traffic = (OZ_TRAFFIC_PER_LAUNCH if (lp == 0 and args.n == 10000 and
-                                             args.prec == "fp64_emu") else None)
-        roof = {"kernel": "ozm_kernel + crt_kernel (Ozaki scheme II FP64 product: 17 modular "
-                          "BF16 tcgen05 products, CRT reconstruction)" +
+        traffic = (OZ_TRAFFIC_PER_LAUNCH if (OZ_TRAFFIC_PER_LAUNCH and lp == 0 and args.n == 10000
+                                             and args.prec == "fp64_emu") else None)
+        roof = {"kernel": "ozm_kernel + crt_group_kernel (Ozaki scheme II FP64 product: 17 modular "
+                          "BF16 tcgen05 products of each of Gauss's three real products, CRT "
+                          "reconstruction)" +
                           (" + tc_filter_bf16x3_kernel" if lp > 0 else ""),
                 "bound": "tensor", "achieved": achieved, "peak": BF16_SUSTAINED_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / BF16_SUSTAINED_TFLOPS if achieved else None,
@@ -722,8 +727,8 @@ def main():
                 "peak_source": "measured: cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
                 "tensor_pipe_tflops": pipe,
                 "frac_tensor_pipe": pipe / BF16_SUSTAINED_TFLOPS if pipe else None,
-                "tensor_pipe_meaning": "BF16 modular products issued (%d per FP64-equivalent flop) "
-                                       "per launch / duration" % OZAKI_PAIRS,
+                "tensor_pipe_meaning": "BF16 modular-product flops issued (%.2f per FP64-equivalent "
+                                       "flop) per launch / duration" % OZAKI_PAIRS,
                 "vs_fp64_dfma_peak": achieved / FP64_PEAK_TFLOPS if achieved else None,
                 "traffic": traffic, "algorithmic_bytes": alg_bytes,
                 "traffic_vs_algorithmic": traffic / alg_bytes if traffic else None}

@@ -390,6 +390,7 @@ __global__ void __launch_bounds__(M_THREADS, 1)
 // Returns the FP64 rounding m of |X| and the sign, with X = m 2^{*shift}.
 // X = sum_j r_j C_j mod P from the residues r_j < p_j, rounded once to FP64: returns the
 // signed magnitude and *shift_out with |X| = |value| 2^shift.
+__device__ __forceinline__ double crt_finish(const unsigned long long* acc, int* shift_out);
 __device__ __forceinline__ double crt_combine(const uint32_t* rj, int* shift_out) {
   unsigned long long acc[5] = {0, 0, 0, 0, 0};
 #pragma unroll
@@ -397,6 +398,12 @@ __device__ __forceinline__ double crt_combine(const uint32_t* rj, int* shift_out
 #pragma unroll
     for (int l = 0; l < 5; ++l) acc[l] += (unsigned long long)rj[j] * c_crt.C[j][l];
   }
+  return crt_finish(acc, shift_out);
+}
+
+// X = (sum_j r_j C_j, accumulated in 32-bit limbs with 64-bit headroom) mod P, rounded once to
+// FP64.
+__device__ __forceinline__ double crt_finish(const unsigned long long* acc, int* shift_out) {
   uint32_t x[5];
   unsigned long long carry = 0;
 #pragma unroll
@@ -500,10 +507,11 @@ __device__ __forceinline__ double crt_value(const uint8_t* __restrict__ R, size_
 __device__ __forceinline__ void crt_store(double x, int sh, int r, int c, const int* __restrict__ rowexp,
                                           const int* __restrict__ colexp, int col0, double alpha,
                                           double beta, const double* X64, double gamma,
-                                          const double* Z64, double* out64, int ldo) {
+                                          const double* Z64, double* out64, int ldo, int er = -1) {
   // x 2^E with |x| in [2^63, 2^64]: one exact multiply by the power of two 2^E built from
-  // its exponent field when that is a normal number (ldexp otherwise)
-  const int E = sh + rowexp[r] + colexp[col0 + c] - 2 * OZ_KBITS;
+  // its exponent field when that is a normal number (ldexp otherwise); er: the row whose
+  // exponent scales the entry (r by default)
+  const int E = sh + rowexp[er < 0 ? r : er] + colexp[col0 + c] - 2 * OZ_KBITS;
   const double v0 = (E > -1022 && E < 1024) ? x * __longlong_as_double((long long)(E + 1023) << 52)
                                             : ldexp(x, E);
   const size_t idx = (size_t)r + (size_t)(col0 + c) * ldo;
@@ -564,6 +572,53 @@ __global__ void __launch_bounds__(256) crt4_kernel(int M, int N, int splits, con
   }
 }
 
+// Reconstruction of one problem in the three-product layout (residues of P1 | P2 | P3, n x N
+// each): four consecutive entries per thread, every residue plane read as 4-byte words;
+// Re = P1 - P2 to stacked row r, Im = P3 - P1 - P2 to row n + r (both scaled by row r).
+__global__ void __launch_bounds__(256) crt3_kernel(int n, int N, const uint8_t* __restrict__ R,
+                                                   const int* __restrict__ rowexp,
+                                                   const int* __restrict__ colexp, int col0,
+                                                   double alpha, double beta, const double* X64,
+                                                   double gamma, const double* Z64, double* out64,
+                                                   int ldo) {
+  const size_t total = (size_t)n * N, quads = total / 4;
+  const uint32_t* R4 = (const uint32_t*)R;
+  const size_t stride4 = total / 4, set4 = (size_t)kOzModuli * stride4;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < quads;
+       q += (size_t)gridDim.x * blockDim.x) {
+    uint32_t w1[kOzModuli], w2[kOzModuli], w3[kOzModuli];
+#pragma unroll
+    for (int j = 0; j < kOzModuli; ++j) {
+      w1[j] = __ldg(R4 + (size_t)j * stride4 + q);
+      w2[j] = __ldg(R4 + set4 + (size_t)j * stride4 + q);
+      w3[j] = __ldg(R4 + 2 * set4 + (size_t)j * stride4 + q);
+    }
+#pragma unroll 1
+    for (int e = 0; e < 4; ++e) {
+      unsigned long long are[5] = {0, 0, 0, 0, 0}, aim[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+      for (int j = 0; j < kOzModuli; ++j) {
+        const uint32_t pj = (uint32_t)oz_modulus(j);
+        const uint32_t r1 = (w1[j] >> (8 * e)) & 0xFFu, r2 = (w2[j] >> (8 * e)) & 0xFFu,
+                       r3 = (w3[j] >> (8 * e)) & 0xFFu;
+        const uint32_t re = (r1 + pj - r2) % pj, im = (r3 + 2 * pj - r1 - r2) % pj;
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+          are[l] += (unsigned long long)re * c_crt.C[j][l];
+          aim[l] += (unsigned long long)im * c_crt.C[j][l];
+        }
+      }
+      const size_t t = 4 * q + e;
+      const int r = (int)(t % n), c = (int)(t / n);
+      int sh;
+      double x = crt_finish(are, &sh);
+      crt_store(x, sh, r, c, rowexp, colexp, col0, alpha, beta, X64, gamma, Z64, out64, ldo);
+      x = crt_finish(aim, &sh);
+      crt_store(x, sh, n + r, c, rowexp, colexp, col0, alpha, beta, X64, gamma, Z64, out64, ldo, r);
+    }
+  }
+}
+
 struct CrtGroupParams {
   const uint8_t* R[kOzGroupMax];
   const int* rowexp[kOzGroupMax];
@@ -574,6 +629,7 @@ struct CrtGroupParams {
   double alpha[kOzGroupMax], beta[kOzGroupMax], gamma[kOzGroupMax];
   long long out0[kOzGroupMax + 1];  // first output index of each problem
   int M[kOzGroupMax], N[kOzGroupMax], col0[kOzGroupMax], ldo[kOzGroupMax];
+  int c3[kOzGroupMax];  // three-product layout: M = n, residues of P1 | P2 | P3, stacked output
   int count;
 };
 static_assert(sizeof(CrtGroupParams) <= 32000, "kernel parameter space");
@@ -591,6 +647,28 @@ __global__ void __launch_bounds__(256) crt_group_kernel(const __grid_constant__ 
     const long long u = t - P.out0[p];
     const int M = P.M[p];
     const int r = (int)(u % M), c = (int)(u / M);
+    if (P.c3[p]) {
+      // Re = P1 - P2 (output row r), Im = P3 - P1 - P2 (row n + r), both scaled by row r
+      const size_t stride_z = (size_t)M * P.N[p], set = (size_t)kOzModuli * stride_z;
+      const uint8_t* R = P.R[p];
+      uint32_t re[kOzModuli], im[kOzModuli];
+#pragma unroll
+      for (int j = 0; j < kOzModuli; ++j) {
+        const uint32_t pj = (uint32_t)oz_modulus(j);
+        const size_t at = (size_t)j * stride_z + (size_t)u;
+        const uint32_t r1 = R[at], r2 = R[set + at], r3 = R[2 * set + at];
+        re[j] = (r1 + pj - r2) % pj;
+        im[j] = (r3 + 2 * pj - r1 - r2) % pj;
+      }
+      int sh;
+      double x = crt_combine(re, &sh);
+      crt_store(x, sh, r, c, P.rowexp[p], P.colexp[p], P.col0[p], P.alpha[p], P.beta[p], P.X64[p],
+                P.gamma[p], P.Z64[p], P.out64[p], P.ldo[p]);
+      x = crt_combine(im, &sh);
+      crt_store(x, sh, M + r, c, P.rowexp[p], P.colexp[p], P.col0[p], P.alpha[p], P.beta[p], P.X64[p],
+                P.gamma[p], P.Z64[p], P.out64[p], P.ldo[p], r);
+      continue;
+    }
     int sh;
     const double x = crt_value(P.R[p], (size_t)M * P.N[p], (size_t)u, 1, &sh);
     const int E = sh + P.rowexp[p][r] + P.colexp[p][P.col0[p] + c] - 2 * OZ_KBITS;
@@ -622,10 +700,8 @@ __device__ __forceinline__ int exp_bound(unsigned long long amax_bits) {
 }
 
 // x_int = round(x 2^{57 - e}) (|x| < 2^e, so |x_int| <= 2^57), from the significand and
-// exponent fields; then its residues mod p_j in symmetric range, stored as BF16 (exact:
-// integers of magnitude <= 128) in plane j.
-__device__ __forceinline__ void write_residues(double x, int e, __nv_bfloat16* base, size_t idx,
-                                               size_t plane) {
+// exponent fields (round half away from zero: the integer of -x is minus that of x).
+__device__ __forceinline__ long long oz_int(double x, int e) {
   const long long bits = __double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   long long m = bits & ((1LL << 52) - 1);
@@ -642,8 +718,15 @@ __device__ __forceinline__ void write_residues(double x, int e, __nv_bfloat16* b
     else if (sh > -64) X = (m + (1LL << (-sh - 1))) >> (-sh);
     if (bits < 0) X = -X;
   }
-  // |X| < 2^58 as two 29-bit halves: |X| mod p = (U1 (2^29 mod p) + U0) mod p in 32-bit
-  // arithmetic (remainders by compile-time constants)
+  return X;
+}
+
+// Residues of an integer X (|X| < 2^59) mod p_j in symmetric range, stored as BF16 (exact:
+// integers of magnitude <= 128) in plane j.
+__device__ __forceinline__ void write_residues_int(long long X, __nv_bfloat16* base, size_t idx,
+                                                   size_t plane) {
+  // |X| as two 30-bit halves: |X| mod p = (U1 (2^29 mod p) + U0) mod p in 32-bit arithmetic
+  // (remainders by compile-time constants)
   const unsigned long long U = (unsigned long long)(X < 0 ? -X : X);
   const uint32_t U1 = (uint32_t)(U >> 29), U0 = (uint32_t)(U & ((1u << 29) - 1));
 #pragma unroll
@@ -656,6 +739,11 @@ __device__ __forceinline__ void write_residues(double x, int e, __nv_bfloat16* b
     else if (rr < -((int)p / 2)) rr += (int)p;
     base[idx + (size_t)j * plane] = __int2bfloat16_rn(rr);  // exact: |rr| <= 128
   }
+}
+
+__device__ __forceinline__ void write_residues(double x, int e, __nv_bfloat16* base, size_t idx,
+                                               size_t plane) {
+  write_residues_int(oz_int(x, e), base, idx, plane);
 }
 
 __device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* red) {
@@ -726,6 +814,70 @@ __global__ void __launch_bounds__(256) oz_slice_V_kernel(int M, int c0, const do
   }
 }
 
+// ---- Gauss's three products for complex operands ----
+// A = Ar + i Ai, V = Vr + i Vi: with the row exponents of A (over Re and Im together) and the
+// column exponents of V as in the stacked form, the integers of Ar, Ai, Vr, Vi are those of
+// the stacked operands, and
+//   P1 = Ar Vr,  P2 = Ai Vi,  P3 = (Ar + Ai)(Vr + Vi)   (exact integer products mod p_j)
+//   Re(A V) = P1 - P2,  Im(A V) = P3 - P1 - P2
+// are the stacked product's two halves as the same integers: three real products of order n
+// instead of one of order 2n (3/4 of the MMA work and of A's residue planes), the same
+// results bit for bit.  The residues of Ar + Ai (|.| <= 2^58) come from the integer sums.
+// Layout: three plane sets (Ar | Ai | Ar + Ai, or Vr | Vi | Vr + Vi), each kOzModuli planes,
+// one after another.
+
+// Row m of A (complex Hermitian, column-major): its three integer rows from column m of A
+// (A[m, k] = conj(A[k, m])): Ar[m, k] = Re A[k, m], Ai[m, k] = -Im A[k, m].
+__global__ void __launch_bounds__(256) oz_slice_A3_kernel(int n, const z64* __restrict__ A, int lda,
+                                                          int kpn, __nv_bfloat16* planes, size_t plane,
+                                                          size_t set, int* rowexp) {
+  __shared__ unsigned long long red[8];
+  const int m = blockIdx.x;
+  const z64* col = A + (size_t)m * lda;
+  unsigned long long amax = 0;
+  for (int k = threadIdx.x; k < n; k += 256) {
+    const unsigned long long b = max(abs_bits(col[k].x), abs_bits(col[k].y));
+    amax = b > amax ? b : amax;
+  }
+  const int e = exp_bound(block_max(amax, red));
+  if (threadIdx.x == 0) rowexp[m] = e;
+  for (int k = threadIdx.x; k < kpn; k += 256) {
+    long long Xr = 0, Xi = 0;
+    if (k < n) {
+      const z64 a = col[k];
+      Xr = oz_int(a.x, e);
+      Xi = -oz_int(a.y, e);
+    }
+    const size_t idx = (size_t)m * kpn + k;
+    write_residues_int(Xr, planes, idx, plane);
+    write_residues_int(Xi, planes + set, idx, plane);
+    write_residues_int(Xr + Xi, planes + 2 * set, idx, plane);
+  }
+}
+
+// Column c of the stacked FP64 block V64 ([Re V; Im V], 2n rows, ld ldi): its exponent over
+// both halves, then the three integer columns (Vr | Vi | Vr + Vi), ld kpn.
+__device__ __forceinline__ void slice_V3_column(int n, int c, const double* __restrict__ V64, int ldi,
+                                                int kpn, __nv_bfloat16* planes, size_t plane, size_t set,
+                                                int* colexp, unsigned long long* red) {
+  const double* col = V64 + (size_t)c * ldi;
+  unsigned long long amax = 0;
+  for (int k = threadIdx.x; k < 2 * n; k += 256) {
+    const unsigned long long b = abs_bits(col[k]);
+    amax = b > amax ? b : amax;
+  }
+  const int e = exp_bound(block_max(amax, red));
+  if (threadIdx.x == 0) colexp[c] = e;
+  for (int k = threadIdx.x; k < kpn; k += 256) {
+    const long long Xr = k < n ? oz_int(col[k], e) : 0;
+    const long long Xi = k < n ? oz_int(col[n + k], e) : 0;
+    const size_t idx = (size_t)c * kpn + k;
+    write_residues_int(Xr, planes, idx, plane);
+    write_residues_int(Xi, planes + set, idx, plane);
+    write_residues_int(Xr + Xi, planes + 2 * set, idx, plane);
+  }
+}
+
 // Grouped form of oz_slice_V_kernel: one block per sliced column of every problem.
 struct SliceGroupParams {
   const double* V64[kOzGroupMax];
@@ -734,6 +886,7 @@ struct SliceGroupParams {
   long long plane[kOzGroupMax];
   int blk0[kOzGroupMax + 1];  // first block of each problem
   int M[kOzGroupMax], c0[kOzGroupMax], ldi[kOzGroupMax], kp[kOzGroupMax];
+  int c3[kOzGroupMax];  // complex problem in the three-product layout (M = n)
   int count;
 };
 static_assert(sizeof(SliceGroupParams) <= 32000, "kernel parameter space");
@@ -744,6 +897,11 @@ __global__ void __launch_bounds__(256) oz_slice_V_group_kernel(const __grid_cons
   while (p + 1 < P.count && (int)blockIdx.x >= P.blk0[p + 1]) ++p;
   const int c = P.c0[p] + (blockIdx.x - P.blk0[p]);
   const int M = P.M[p], kp = P.kp[p];
+  if (P.c3[p]) {
+    slice_V3_column(M, c, P.V64[p], P.ldi[p], kp, P.planes[p], (size_t)P.plane[p],
+                    (size_t)kOzModuli * P.plane[p], P.colexp[p], red);
+    return;
+  }
   const double* col = P.V64[p] + (size_t)c * P.ldi[p];
   unsigned long long amax = 0;
   for (int k = threadIdx.x; k < M; k += 256) {
@@ -937,6 +1095,16 @@ int oz_slice_A(cudaStream_t st, int n, const T* A, int lda, int kp, void* planes
   return 0;
 }
 
+int oz_slice_A3(cudaStream_t st, int n, const z64* A, int lda, int kpn, void* planes, int* rowexp,
+                int* launches) {
+  const size_t plane = (size_t)n * kpn;
+  oz_slice_A3_kernel<<<n, 256, 0, st>>>(n, A, lda, kpn, (__nv_bfloat16*)planes, plane,
+                                        (size_t)kOzModuli * plane, rowexp);
+  if (launches) ++*launches;
+  CHASE_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
 int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ldi, int kp,
                int ncols_total, void* planes, int* colexp, int* launches) {
   if (c1 <= c0) return 0;
@@ -1089,6 +1257,7 @@ int oz_slice_V_group(cudaStream_t st, int count, const OzGroupItem* items, int* 
       P.c0[p] = it.col0;
       P.ldi[p] = it.ldi;
       P.kp[p] = it.kp;
+      P.c3[p] = it.c3;
       blocks += it.N;
     }
     if (P.count == 0) continue;
@@ -1102,28 +1271,55 @@ int oz_slice_V_group(cudaStream_t st, int count, const OzGroupItem* items, int* 
 
 int oz_gemm_group(cudaStream_t st, int count, const OzGroupItem* items, DevStatus* dst, int* launches) {
   CHASE_CUDA_TRY(cudaFuncSetAttribute(ozm_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM));
-  for (int g0 = 0; g0 < count; g0 += kOzGroupMax) {
-    const int cnt = std::min(kOzGroupMax, count - g0);
-    OzmGroupParams P{};
-    CrtGroupParams C{};
-    int tiles = 0;
-    long long outs = 0;
-    P.count = 0;
-    for (int i = 0; i < cnt; ++i) {
-      const OzGroupItem& it = items[g0 + i];
-      if (it.N <= 0 || it.M <= 0) continue;
-      if (it.kp % MBK != 0 || it.kp > kOzMaxK) return CHASE_ERR_UNSUPPORTED;
-      if ((size_t)kOzModuli * it.M * it.N > it.resbuf.bytes) return CHASE_ERR_OOM;
+  OzmGroupParams P{};
+  CrtGroupParams C{};
+  int tiles = 0;
+  long long outs = 0;
+  // one launch of the modular products and one of the reconstructions for what is gathered
+  auto flush = [&]() -> int {
+    if (P.count == 0) return 0;
+    P.tile0[P.count] = tiles;
+    C.out0[C.count] = outs;
+    TRY_OZ(launch_pairs(ozm_group_kernel, dim3(tiles, 1, kOzModuli), st, P, dst));
+    if (launches) ++*launches;
+    if (C.count == 1 && C.c3[0] && outs % 4 == 0) {  // one complex problem: the vector form
+      const int b4 = (int)std::max<long long>(1, std::min<long long>((outs / 4 + 255) / 256, (long long)kNumSMs * 16));
+      crt3_kernel<<<b4, 256, 0, st>>>(C.M[0], C.N[0], C.R[0], C.rowexp[0], C.colexp[0], C.col0[0],
+                                      C.alpha[0], C.beta[0], C.X64[0], C.gamma[0], C.Z64[0],
+                                      C.out64[0], C.ldo[0]);
+    } else {
+      const int blocks = (int)std::max<long long>(1, std::min<long long>((outs + 255) / 256, (long long)kNumSMs * 16));
+      crt_group_kernel<<<blocks, 256, 0, st>>>(C);
+    }
+    if (launches) ++*launches;
+    CHASE_CUDA_TRY(cudaGetLastError());
+    P = OzmGroupParams{};
+    C = CrtGroupParams{};
+    tiles = 0;
+    outs = 0;
+    return 0;
+  };
+  for (int i = 0; i < count; ++i) {
+    const OzGroupItem& it = items[i];
+    if (it.N <= 0 || it.M <= 0) continue;
+    if (it.kp % MBK != 0 || it.kp > kOzMaxK) return CHASE_ERR_UNSUPPORTED;
+    const int sets = it.c3 ? 3 : 1;  // three-product layout: P1, P2, P3
+    if ((size_t)sets * kOzModuli * it.M * it.N > it.resbuf.bytes) return CHASE_ERR_OOM;
+    if (P.count + sets > kOzGroupMax || C.count + 1 > kOzGroupMax) TRY_OZ(flush());
+    OzPlan plan;  // the autotuner's tile width for this shape, if it measured one
+    oz_plan_lookup(it.M, it.N, it.kp, &plan);
+    const int ntile = ceil_div(it.N, std::min(plan.bn_max, MBN_MAX));
+    const int BN = ceil_div(ceil_div(it.N, ntile), 16) * 16;
+    const int rows = std::max(it.a_plane_rows, it.M);
+    const size_t aset = (size_t)kOzModuli * rows * it.kp * 2;             // bytes of one A plane set
+    const size_t vset = (size_t)kOzModuli * it.ncols_total * it.kp * 2;   // of one V plane set
+    for (int sidx = 0; sidx < sets; ++sidx) {
       const int p = P.count++;
-      OzPlan plan;  // the autotuner's tile width for this shape, if it measured one
-      oz_plan_lookup(it.M, it.N, it.kp, &plan);
-      const int ntile = ceil_div(it.N, std::min(plan.bn_max, MBN_MAX));
-      const int BN = ceil_div(ceil_div(it.N, ntile), 16) * 16;
-      const int rows = std::max(it.a_plane_rows, it.M);
-      if (make_map3(&P.mapA[p], it.Aplanes, it.kp, it.M, rows, MBM) ||
-          make_map3(&P.mapV[p], it.Vplanes, it.kp, it.ncols_total, it.ncols_total, BN / 2))
+      if (make_map3(&P.mapA[p], (const char*)it.Aplanes + sidx * aset, it.kp, it.M, rows, MBM) ||
+          make_map3(&P.mapV[p], (const char*)it.Vplanes + sidx * vset, it.kp, it.ncols_total,
+                    it.ncols_total, BN / 2))
         return CHASE_ERR_CUDA;
-      P.R[p] = (uint8_t*)it.resbuf.ptr;
+      P.R[p] = (uint8_t*)it.resbuf.ptr + (size_t)sidx * kOzModuli * it.M * it.N;
       P.tile0[p] = tiles;
       P.M[p] = it.M;
       P.N[p] = it.N;
@@ -1132,34 +1328,26 @@ int oz_gemm_group(cudaStream_t st, int count, const OzGroupItem* items, DevStatu
       P.ntile[p] = ntile;
       P.nkb[p] = it.kp / MBK;
       tiles += ntile * ceil_div(it.M, 2 * MBM) * 2;  // CTA pairs over 256-row blocks
-      C.R[p] = (const uint8_t*)it.resbuf.ptr;
-      C.rowexp[p] = it.rowexp;
-      C.colexp[p] = it.colexp;
-      C.X64[p] = it.X64;
-      C.Z64[p] = it.Z64;
-      C.out64[p] = it.out64;
-      C.alpha[p] = it.alpha;
-      C.beta[p] = it.beta;
-      C.gamma[p] = it.gamma;
-      C.out0[p] = outs;
-      C.M[p] = it.M;
-      C.N[p] = it.N;
-      C.col0[p] = it.col0;
-      C.ldo[p] = it.ldo;
-      outs += (long long)it.M * it.N;
     }
-    if (P.count == 0) continue;
-    P.tile0[P.count] = tiles;
-    C.count = P.count;
-    C.out0[C.count] = outs;
-    TRY_OZ(launch_pairs(ozm_group_kernel, dim3(tiles, 1, kOzModuli), st, P, dst));
-    if (launches) ++*launches;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>((outs + 255) / 256, (long long)kNumSMs * 16));
-    crt_group_kernel<<<blocks, 256, 0, st>>>(C);
-    if (launches) ++*launches;
-    CHASE_CUDA_TRY(cudaGetLastError());
+    const int c = C.count++;
+    C.R[c] = (const uint8_t*)it.resbuf.ptr;
+    C.rowexp[c] = it.rowexp;
+    C.colexp[c] = it.colexp;
+    C.X64[c] = it.X64;
+    C.Z64[c] = it.Z64;
+    C.out64[c] = it.out64;
+    C.alpha[c] = it.alpha;
+    C.beta[c] = it.beta;
+    C.gamma[c] = it.gamma;
+    C.out0[c] = outs;
+    C.M[c] = it.M;
+    C.N[c] = it.N;
+    C.col0[c] = it.col0;
+    C.ldo[c] = it.ldo;
+    C.c3[c] = it.c3;
+    outs += (long long)it.M * it.N;
   }
-  return 0;
+  return flush();
 }
 
 template <class T>

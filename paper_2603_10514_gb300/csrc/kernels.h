@@ -126,6 +126,11 @@ size_t oz_residue_bytes(int M, int N);
 template <class T>
 int oz_slice_A(cudaStream_t st, int n, const T* A, int lda, int kp, void* planes, int* rowexp,
                int* launches);
+// Complex A (n x n, Hermitian, column-major) into the three-product layout: plane sets
+// Re A | Im A | Re A + Im A, each kOzModuli planes of n x kpn (row-major, K contiguous),
+// row exponents over Re and Im together (those of the stacked form).
+int oz_slice_A3(cudaStream_t st, int n, const z64* A, int lda, int kpn, void* planes, int* rowexp,
+                int* launches);
 int oz_slice_V(cudaStream_t st, int M, int c0, int c1, const double* V64, int ldi, int kp,
                int ncols_total, void* planes, int* colexp, int* launches);
 template <class T>
@@ -188,6 +193,9 @@ struct OzGroupItem {
   Scratch resbuf{nullptr, 0};
   const double* V64_in = nullptr;
   int ldi = 0;
+  // complex problem in the three-product layout: M = n, Aplanes / Vplanes hold three plane
+  // sets (Re | Im | Re + Im), V64_in / X64 / Z64 / out64 are the stacked [Re; Im] blocks
+  int c3 = 0;
 };
 int oz_slice_V_group(cudaStream_t st, int count, const OzGroupItem* items, int* launches);
 int oz_gemm_group(cudaStream_t st, int count, const OzGroupItem* items, DevStatus* dst, int* launches);

@@ -320,7 +320,10 @@ int filter_mixed(chase_ctx* h, int n, const T* A, int lda, bool split_A, int nco
 // A (prepared once per call site) and of the current block.
 // ---------------------------------------------------------------------------
 struct OzBufs {
-  int M = 0, kp = 0, ncols = 0;
+  int M = 0, kp = 0, ncols = 0;  // stacked FP64 blocks: M rows, ld kp
+  // complex problems: the three-product layout (Gauss): A and V planes as Re | Im | Re + Im
+  // sets of n rows (K padded to kpn); the FP64 blocks stay stacked
+  int c3 = 0, n = 0, kpn = 0;
   void* Ap = nullptr;
   int* rowexp = nullptr;
   void* Vp = nullptr;
@@ -333,7 +336,11 @@ template <class T>
 size_t oz_bytes(int n, int ncols) {
   const int M = Sc<T>::cplx ? 2 * n : n;
   const size_t kp = (size_t)tc_kpad(M);
-  return align256(kOzPlaneBytes * (size_t)M * kp) + align256(4 * (size_t)M) + align256(kOzPlaneBytes * kp * ncols) +
+  // plane rows x K of A and K x columns of V: stacked (real) or three sets of order n (complex)
+  const size_t arows = Sc<T>::cplx ? 3 * (size_t)n : (size_t)M;
+  const size_t ak = Sc<T>::cplx ? (size_t)tc_kpad(n) : kp;
+  const size_t vk = Sc<T>::cplx ? 3 * (size_t)tc_kpad(n) : kp;
+  return align256(kOzPlaneBytes * arows * ak) + align256(4 * (size_t)M) + align256(kOzPlaneBytes * vk * ncols) +
          align256(4 * (size_t)ncols) + 2 * align256(8 * kp * ncols) + align256(oz_residue_bytes((int)kp, ncols));
 }
 
@@ -343,15 +350,60 @@ OzBufs oz_carve(char* base, int n, int ncols) {
   B.M = Sc<T>::cplx ? 2 * n : n;
   B.kp = tc_kpad(B.M);
   B.ncols = ncols;
+  B.c3 = Sc<T>::cplx ? 1 : 0;
+  B.n = n;
+  B.kpn = tc_kpad(n);
+  const size_t arows = B.c3 ? 3 * (size_t)n : (size_t)B.M;
+  const size_t ak = B.c3 ? (size_t)B.kpn : (size_t)B.kp;
+  const size_t vk = B.c3 ? 3 * (size_t)B.kpn : (size_t)B.kp;
   size_t off = 0;
-  B.Ap = base + off; off += align256(kOzPlaneBytes * (size_t)B.M * B.kp);
+  B.Ap = base + off; off += align256(kOzPlaneBytes * arows * ak);
   B.rowexp = (int*)(base + off); off += align256(4 * (size_t)B.M);
-  B.Vp = base + off; off += align256(kOzPlaneBytes * (size_t)B.kp * ncols);
+  B.Vp = base + off; off += align256(kOzPlaneBytes * vk * ncols);
   B.colexp = (int*)(base + off); off += align256(4 * (size_t)ncols);
   for (int i = 0; i < 2; ++i) { B.V64[i] = (double*)(base + off); off += align256(8 * (size_t)B.kp * ncols); }
   B.res = Scratch{base + off, oz_residue_bytes(B.kp, ncols)};
   off += align256(oz_residue_bytes(B.kp, ncols));
   return B;
+}
+
+// A's planes in the layout of B (three-product sets for complex problems, stacked otherwise).
+template <class T>
+int oz_slice_A_bufs(chase_ctx* h, int n, const T* A, int lda, OzBufs& B) {
+  if constexpr (Sc<T>::cplx) {
+    if (B.c3) return oz_slice_A3(h->stream, n, A, lda, B.kpn, B.Ap, B.rowexp, &h->launches);
+  }
+  return oz_slice_A<T>(h->stream, n, A, lda, B.kp, B.Ap, B.rowexp, &h->launches);
+}
+
+// A grouped-product item of B's operands: out64 = alpha A V64_in[:, col0 .. col0 + N) +
+// beta X64 + gamma Z64 (stacked blocks, ld B.kp).
+inline OzGroupItem oz_item(const OzBufs& B, int ncols_total, int col0, int N, double alpha, double beta,
+                           const double* X64, double gamma, const double* Z64, double* out64,
+                           const double* V64_in) {
+  OzGroupItem it;
+  it.c3 = B.c3;
+  it.M = B.c3 ? B.n : B.M;
+  it.kp = B.c3 ? B.kpn : B.kp;
+  it.a_plane_rows = it.M;
+  it.Aplanes = B.Ap;
+  it.rowexp = B.rowexp;
+  it.Vplanes = B.Vp;
+  it.colexp = B.colexp;
+  it.ncols_total = ncols_total;
+  it.col0 = col0;
+  it.N = N;
+  it.alpha = alpha;
+  it.beta = beta;
+  it.gamma = gamma;
+  it.X64 = X64;
+  it.Z64 = Z64;
+  it.out64 = out64;
+  it.ldo = B.kp;
+  it.resbuf = B.res;
+  it.V64_in = V64_in;
+  it.ldi = B.kp;
+  return it;
 }
 
 // Enqueues the whole filter (no host synchronisation: it can be captured into a graph).
@@ -362,7 +414,7 @@ int filter_oz_enqueue(chase_ctx* h, int n, const T* A, int lda, bool split_A, in
   cudaStream_t st = h->stream;
   if (ncols <= 0) return 0;
   const int M = B.M, kp = B.kp;
-  if (split_A) TRY(oz_slice_A<T>(st, n, A, lda, kp, B.Ap, B.rowexp, &h->launches));
+  if (split_A) TRY(oz_slice_A_bufs<T>(h, n, A, lda, B));
   TRY(oz_stack_V<T>(st, n, ncols, V, ldv, B.V64[0], kp, &h->launches));
   CHASE_CUDA_TRY(cudaMemsetAsync(&h->dstat->timeout, 0, sizeof(int), st));
   const int mmax = deg[ncols - 1];
@@ -386,12 +438,21 @@ int filter_oz_enqueue(chase_ctx* h, int n, const T* A, int lda, bool split_A, in
       gamma = -sigma * sn;
       sigma = sn;
     }
-    TRY(oz_slice_V(st, M, first, ncols, B.V64[in], kp, kp, ncols, B.Vp, B.colexp, &h->launches));
-    h->product_timer.begin(st);
-    TRY(oz_gemm(st, M, kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, ncols, first, act, alpha, beta,
-                B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, B.res, &h->launches,
-                h->autotune, &h->tune_trials));
-    h->product_timer.end(st);
+    if (B.c3) {
+      const OzGroupItem it = oz_item(B, ncols, first, act, alpha, beta, B.V64[in], gamma, B.V64[out],
+                                     B.V64[out], B.V64[in]);
+      TRY(oz_slice_V_group(st, 1, &it, &h->launches));
+      h->product_timer.begin(st);
+      TRY(oz_gemm_group(st, 1, &it, h->dstat, &h->launches));
+      h->product_timer.end(st);
+    } else {
+      TRY(oz_slice_V(st, M, first, ncols, B.V64[in], kp, kp, ncols, B.Vp, B.colexp, &h->launches));
+      h->product_timer.begin(st);
+      TRY(oz_gemm(st, M, kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, ncols, first, act, alpha, beta,
+                  B.V64[in], gamma, B.V64[out], B.V64[out], kp, h->dstat, B.res, &h->launches,
+                  h->autotune, &h->tune_trials));
+      h->product_timer.end(st);
+    }
     if (flops) *flops += per_col * act;
     if (steps) ++*steps;
   }
@@ -474,10 +535,16 @@ int aq_oz(chase_ctx* h, int n, const T* Q, int nu, T* AQ, OzBufs& B, Scratch scr
   cudaStream_t st = h->stream;
   if (nu <= 0) return 0;
   TRY(oz_stack_V<T>(st, n, nu, Q, n, B.V64[0], B.kp, &h->launches));
-  TRY(oz_slice_V(st, B.M, 0, nu, B.V64[0], B.kp, B.kp, B.ncols, B.Vp, B.colexp, &h->launches));
-  TRY(oz_gemm(st, B.M, B.kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, B.ncols, 0, nu, 1.0, 0.0, nullptr,
-              0.0, nullptr, B.V64[1], B.kp, h->dstat, B.res, &h->launches, h->autotune,
-              &h->tune_trials));
+  if (B.c3) {
+    const OzGroupItem it = oz_item(B, B.ncols, 0, nu, 1.0, 0.0, nullptr, 0.0, nullptr, B.V64[1], B.V64[0]);
+    TRY(oz_slice_V_group(st, 1, &it, &h->launches));
+    TRY(oz_gemm_group(st, 1, &it, h->dstat, &h->launches));
+  } else {
+    TRY(oz_slice_V(st, B.M, 0, nu, B.V64[0], B.kp, B.kp, B.ncols, B.Vp, B.colexp, &h->launches));
+    TRY(oz_gemm(st, B.M, B.kp, B.Ap, B.rowexp, 0, B.Vp, B.colexp, B.ncols, 0, nu, 1.0, 0.0, nullptr,
+                0.0, nullptr, B.V64[1], B.kp, h->dstat, B.res, &h->launches, h->autotune,
+                &h->tune_trials));
+  }
   TRY(tc_unstack_V<T>(st, n, 0, nu, B.V64[1], B.kp, AQ, n, &h->launches));
   return 0;
 }
@@ -985,7 +1052,7 @@ struct Solve final : SolveBase {
   int group_filter_prepare(GroupFilterItem* g) override {
     interval();
     const int nu = l - k;
-    if (!A_oz) TRY(oz_slice_A<T>(st, n, A, lda, ozb.kp, ozb.Ap, ozb.rowexp, &h->launches));
+    if (!A_oz) TRY(oz_slice_A_bufs<T>(h, n, A, lda, ozb));
     A_oz = true;
     TRY(oz_stack_V<T>(st, n, nu, V + (size_t)k * n, n, ozb.V64[0], ozb.kp, &h->launches));
     g->B = &ozb;
@@ -1046,7 +1113,7 @@ struct Solve final : SolveBase {
     phase_begin();
     T* Q2 = V + (size_t)k * n;
     if (emu) {
-      if (!A_oz) rc = oz_slice_A<T>(st, n, A, lda, ozb.kp, ozb.Ap, ozb.rowexp, &h->launches);
+      if (!A_oz) rc = oz_slice_A_bufs<T>(h, n, A, lda, ozb);
       A_oz = true;
       if (!rc) rc = aq_oz<T>(h, n, Q2, nu, AQ, ozb, scr);
     } else {
@@ -1284,28 +1351,8 @@ int group_filter_oz(chase_ctx* h, const std::vector<SolveBase*>& probs) {
         sigma[p] = sn;
       }
       const OzBufs& B = *q.B;
-      OzGroupItem it;
-      it.M = B.M;
-      it.kp = B.kp;
-      it.a_plane_rows = B.M;
-      it.Aplanes = B.Ap;
-      it.rowexp = B.rowexp;
-      it.Vplanes = B.Vp;
-      it.colexp = B.colexp;
-      it.ncols_total = q.ncols;
-      it.col0 = first[p];
-      it.N = q.ncols - first[p];
-      it.alpha = alpha;
-      it.beta = beta;
-      it.gamma = gamma;
-      it.X64 = B.V64[in];
-      it.Z64 = B.V64[out];
-      it.out64 = B.V64[out];
-      it.ldo = B.kp;
-      it.resbuf = B.res;
-      it.V64_in = B.V64[in];
-      it.ldi = B.kp;
-      items.push_back(it);
+      items.push_back(oz_item(B, q.ncols, first[p], q.ncols - first[p], alpha, beta, B.V64[in], gamma,
+                              B.V64[out], B.V64[out], B.V64[in]));
     }
     rc = oz_slice_V_group(st, (int)items.size(), items.data(), &launches);
     if (!rc) rc = oz_gemm_group(st, (int)items.size(), items.data(), h->dstat, &launches);
