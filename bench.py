@@ -54,9 +54,11 @@ BF16_PEAK_TFLOPS, BF16_SUSTAINED_TFLOPS = _measured_peaks()
 OZAKI_MODULI = 17
 OZAKI_PAIRS = OZAKI_MODULI * 0.75   # the default workload is complex
 # DRAM bytes (read + write) of one emulated product of the default workload (complex
-# n = 10000, 600 active columns): none measured for the three-product form yet (the stacked
-# form's capture, 16.3 GB per product, no longer applies).
-OZ_TRAFFIC_PER_LAUNCH = None
+# n = 10000, 600 active columns), measured by one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, 1 pass): the grouped modular products of the three real products
+# 12.12 GB read and 0.456 GB written; the reconstruction 0.404 GB read and 0.076 GB written.
+# Launches with fewer active columns read the same residue planes of A, which are most of it.
+OZ_TRAFFIC_PER_LAUNCH = 12.125e9 + 0.456e9 + 0.404e9 + 0.076e9
 # Column MatVecs of one complete solve of the default workload as counted by the GPU path
 # (filter MatVecs plus the 2 (ell - k) products of Rayleigh-Ritz and residuals per
 # iteration); used to scale the oracle's timed sample to a whole solve.  Measured on a
