@@ -52,6 +52,9 @@ typedef enum { CHASE_R64 = 0, CHASE_C128 = 1 } chase_dtype;
  *                   remainder theorem, then rounded once to FP64; accurate to
  *                   ~2^-57 K max|A_m.| max|V_.c| per entry, the class of an FP64 product
  *                   (inner dimension up to 2^17: complex n <= 65536, real n <= 131072).
+ *                   Complex A*V and A*Q run as three real products (A_r V_r, A_i V_i,
+ *                   (A_r + A_i)(V_r + V_i)) of the same integers: the same results as one
+ *                   product of the stacked real operator, for 3/4 of its work.
  *   CHASE_BF16X3    mixed: BF16x3 filter products (three BF16 tensor-core
  *                   products of hi/lo splits, FP32 accumulation) while the
  *                   residuals are large, then as CHASE_FP64_EMU.
