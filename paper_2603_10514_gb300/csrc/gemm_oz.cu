@@ -741,6 +741,47 @@ __device__ __forceinline__ void write_residues_int(long long X, __nv_bfloat16* b
   }
 }
 
+// The symmetric residues of X (|X| < 2^59) mod p_j as small integers (|r| <= 128).
+__device__ __forceinline__ void residues_of(long long X, int* r) {
+  const unsigned long long U = (unsigned long long)(X < 0 ? -X : X);
+  const uint32_t U1 = (uint32_t)(U >> 29), U0 = (uint32_t)(U & ((1u << 29) - 1));
+#pragma unroll
+  for (int j = 0; j < kOzModuli; ++j) {
+    const uint32_t p = (uint32_t)oz_modulus(j);
+    const uint32_t k29 = (uint32_t)((1ull << 29) % p);
+    const uint32_t u = ((U1 % p) * k29 + U0 % p) % p;
+    int rr = X < 0 ? -(int)u : (int)u;
+    if (rr > (int)p / 2) rr -= (int)p;
+    else if (rr < -((int)p / 2)) rr += (int)p;
+    r[j] = rr;
+  }
+}
+
+// Residues of two adjacent K entries (idx, idx + 1) of three plane sets: the parts' integers
+// Xr, Xi and their sum, whose residue is the sum of the parts' residues brought back into the
+// symmetric range (a representative of the same class: the modular products use only the
+// class, and |r| <= 128 keeps their K chunks exact).  Stored as BF16 pairs.
+__device__ __forceinline__ void write_residues3_pair(long long xr0, long long xi0, long long xr1,
+                                                     long long xi1, __nv_bfloat16* base, size_t idx,
+                                                     size_t plane, size_t set) {
+  int a0[kOzModuli], b0[kOzModuli], a1[kOzModuli], b1[kOzModuli];
+  residues_of(xr0, a0);
+  residues_of(xi0, b0);
+  residues_of(xr1, a1);
+  residues_of(xi1, b1);
+#pragma unroll
+  for (int j = 0; j < kOzModuli; ++j) {
+    const int p = oz_modulus(j);
+    int s0 = a0[j] + b0[j], s1 = a1[j] + b1[j];
+    if (s0 > p / 2) s0 -= p; else if (s0 < -(p / 2)) s0 += p;
+    if (s1 > p / 2) s1 -= p; else if (s1 < -(p / 2)) s1 += p;
+    const size_t at = idx + (size_t)j * plane;
+    *(__nv_bfloat162*)(base + at) = __nv_bfloat162(__int2bfloat16_rn(a0[j]), __int2bfloat16_rn(a1[j]));
+    *(__nv_bfloat162*)(base + set + at) = __nv_bfloat162(__int2bfloat16_rn(b0[j]), __int2bfloat16_rn(b1[j]));
+    *(__nv_bfloat162*)(base + 2 * set + at) = __nv_bfloat162(__int2bfloat16_rn(s0), __int2bfloat16_rn(s1));
+  }
+}
+
 __device__ __forceinline__ void write_residues(double x, int e, __nv_bfloat16* base, size_t idx,
                                                size_t plane) {
   write_residues_int(oz_int(x, e), base, idx, plane);
@@ -841,17 +882,17 @@ __global__ void __launch_bounds__(256) oz_slice_A3_kernel(int n, const z64* __re
   }
   const int e = exp_bound(block_max(amax, red));
   if (threadIdx.x == 0) rowexp[m] = e;
-  for (int k = threadIdx.x; k < kpn; k += 256) {
-    long long Xr = 0, Xi = 0;
-    if (k < n) {
-      const z64 a = col[k];
-      Xr = oz_int(a.x, e);
-      Xi = -oz_int(a.y, e);
+  for (int k = 2 * threadIdx.x; k < kpn; k += 512) {  // kpn is even: pairs (k, k + 1)
+    long long xr[2] = {0, 0}, xi[2] = {0, 0};
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      if (k + d < n) {
+        const z64 a = col[k + d];
+        xr[d] = oz_int(a.x, e);
+        xi[d] = -oz_int(a.y, e);
+      }
     }
-    const size_t idx = (size_t)m * kpn + k;
-    write_residues_int(Xr, planes, idx, plane);
-    write_residues_int(Xi, planes + set, idx, plane);
-    write_residues_int(Xr + Xi, planes + 2 * set, idx, plane);
+    write_residues3_pair(xr[0], xi[0], xr[1], xi[1], planes, (size_t)m * kpn + k, plane, set);
   }
 }
 
@@ -868,13 +909,16 @@ __device__ __forceinline__ void slice_V3_column(int n, int c, const double* __re
   }
   const int e = exp_bound(block_max(amax, red));
   if (threadIdx.x == 0) colexp[c] = e;
-  for (int k = threadIdx.x; k < kpn; k += 256) {
-    const long long Xr = k < n ? oz_int(col[k], e) : 0;
-    const long long Xi = k < n ? oz_int(col[n + k], e) : 0;
-    const size_t idx = (size_t)c * kpn + k;
-    write_residues_int(Xr, planes, idx, plane);
-    write_residues_int(Xi, planes + set, idx, plane);
-    write_residues_int(Xr + Xi, planes + 2 * set, idx, plane);
+  for (int k = 2 * threadIdx.x; k < kpn; k += 512) {  // kpn is even: pairs (k, k + 1)
+    long long xr[2] = {0, 0}, xi[2] = {0, 0};
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      if (k + d < n) {
+        xr[d] = oz_int(col[k + d], e);
+        xi[d] = oz_int(col[n + k + d], e);
+      }
+    }
+    write_residues3_pair(xr[0], xi[0], xr[1], xi[1], planes, (size_t)c * kpn + k, plane, set);
   }
 }
 
