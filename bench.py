@@ -718,7 +718,7 @@ def main():
         pipe = tc_flops / nl / dur_launch / 1e12 if dur_launch > 0 else None
         traffic = (OZ_TRAFFIC_PER_LAUNCH if (OZ_TRAFFIC_PER_LAUNCH and lp == 0 and args.n == 10000
                                              and args.prec == "fp64_emu") else None)
-        roof = {"kernel": "ozm_kernel + crt_group_kernel (Ozaki scheme II FP64 product: 17 modular "
+        roof = {"kernel": "ozm_group_kernel + crt3_kernel (Ozaki scheme II FP64 product: 17 modular "
                           "BF16 tcgen05 products of each of Gauss's three real products, CRT "
                           "reconstruction)" +
                           (" + tc_filter_bf16x3_kernel" if lp > 0 else ""),
