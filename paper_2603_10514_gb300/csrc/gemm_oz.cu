@@ -145,6 +145,29 @@ constexpr CrtTable make_crt_table() {
 
 __constant__ CrtTable c_crt = make_crt_table();
 
+// Compile-time checks of the number theory the reconstruction relies on: the moduli are
+// pairwise coprime, C_j is 1 mod p_j and 0 mod every other modulus, and P exceeds twice the
+// largest integer product, 2 * 2^17 * 2^114 = 2^132 (limb 4 holds P / 2^128).
+constexpr int oz_gcd(int a, int b) { return b == 0 ? a : oz_gcd(b, a % b); }
+constexpr bool oz_moduli_coprime() {
+  for (int i = 0; i < kOzModuli; ++i)
+    for (int j = i + 1; j < kOzModuli; ++j)
+      if (oz_gcd(oz_modulus(i), oz_modulus(j)) != 1) return false;
+  return true;
+}
+constexpr bool oz_crt_basis_ok() {
+  const CrtTable t = make_crt_table();
+  for (int j = 0; j < kOzModuli; ++j) {
+    const Big Cj{{t.C[j][0], t.C[j][1], t.C[j][2], t.C[j][3], t.C[j][4]}};
+    for (int i = 0; i < kOzModuli; ++i)
+      if (big_mod_small(Cj, (uint32_t)oz_modulus(i)) != (i == j ? 1u : 0u)) return false;
+  }
+  return true;
+}
+static_assert(oz_moduli_coprime(), "moduli must be pairwise coprime");
+static_assert(oz_crt_basis_ok(), "CRT basis: C_j = 1 mod p_j, 0 mod p_i");
+static_assert(make_crt_table().P[4] >= (1u << (2 * OZ_KBITS + 17 + 1 - 128)), "P > 2 K 2^114");
+
 constexpr int MBM = 128, MBK = 64;
 constexpr int MKS = 2;             // 64-wide K blocks per stage: 8 MMAs per barrier round trip
 constexpr int MNST = 3;            // stages
