@@ -295,7 +295,8 @@ int chase_lanczos_bounds(chase_handle h, chase_dtype dtype, int n, const void* d
  * for slow ones.
  * Each problem's arithmetic is the one chase_solve performs (the grouped products are exact
  * integer products like the single ones), so results are identical to chase_solve's.  Problems
- * with other precisions, or with graph_filter = 1, filter one by one inside the same step.
+ * with other precisions, with graph_filter = 1 or with n > 65536, filter one by one inside the
+ * same step.
  * Problems may be added between steps (a service admits requests as earlier ones finish).
  * Device workspace comes from a caching pool owned by the session.
  */

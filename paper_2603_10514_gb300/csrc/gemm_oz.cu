@@ -167,6 +167,18 @@ constexpr bool oz_crt_basis_ok() {
 static_assert(oz_moduli_coprime(), "moduli must be pairwise coprime");
 static_assert(oz_crt_basis_ok(), "CRT basis: C_j = 1 mod p_j, 0 mod p_i");
 static_assert(make_crt_table().P[4] >= (1u << (2 * OZ_KBITS + 17 + 1 - 128)), "P > 2 K 2^114");
+// The modular epilogue reduces a split's sum |s| <= kOzSplitMaxK * 128^2 = 2^30 with the
+// float quotient q = floor(fl(fl(s) * fl(1/p))): fl(s) is within 32 of s and the two roundings
+// add a relative 2^-23, so q is within 32/p + 2^30 2^-23 / p < 1 of s/p for p > 160 and one
+// correction step lands in [0, p).
+constexpr bool oz_moduli_above(int lo) {
+  for (int j = 0; j < kOzModuli; ++j)
+    if (oz_modulus(j) <= lo) return false;
+  return true;
+}
+static_assert(oz_moduli_above(160), "epilogue reduction: p > 160");
+static_assert((long long)kOzSplitMaxK * 128 * 128 <= (1ll << 30), "epilogue reduction: |sum| <= 2^30");
+static_assert(kOzMaxK <= kOzMaxSplits * kOzSplitMaxK, "every admissible K fits the splits");
 
 constexpr int MBM = 128, MBK = 64;
 constexpr int MKS = 2;             // 64-wide K blocks per stage: 8 MMAs per barrier round trip
@@ -329,7 +341,8 @@ __device__ __forceinline__ void ozm_pair_tile(const CUtensorMap* mapA, const CUt
       }
     }
     if (__shfl_sync(0xffffffffu, (int)(ok && !*(volatile int*)s_err), 0) && r < M) {
-      // sum mod p in [0, p): the float quotient of |sum| < 2^29 is off by at most one
+      // sum mod p in [0, p): |sum| <= 2^30 (K <= kOzSplitMaxK per split), so the float quotient is
+      // off by at most one
       const int pm = c_crt.p[jm];
       const float ip = 1.0f / (float)pm;
 #pragma unroll
@@ -1225,9 +1238,11 @@ int ozm_launch(cudaStream_t st, int M, int kp, const void* Aplanes, int a_plane_
   const int nchunks = ceil_div(nkb, kChunkKB);
   int S = std::max(1, std::min(nchunks, ceil_div(4 * kNumSMs, ntile * mblk * kOzModuli)));
   if (plan.splits > 0) S = std::min(plan.splits, nchunks);
-  S = std::min(S, kOzMaxSplits);
-  while (S > 1 && (size_t)S * slab > resbuf.bytes) --S;
-  if (slab > resbuf.bytes) return CHASE_ERR_OOM;
+  // no split longer than kOzSplitMaxK (the range of the epilogue's exact reduction)
+  const int min_S = ceil_div(nchunks, kOzSplitMaxK / 1024);
+  S = std::max(std::min(S, kOzMaxSplits), min_S);
+  while (S > min_S && (size_t)S * slab > resbuf.bytes) --S;
+  if ((size_t)S * slab > resbuf.bytes) return CHASE_ERR_OOM;
   const int kbs = ceil_div(nchunks, S) * kChunkKB;  // whole chunks: every split starts on an even block
   S = ceil_div(nkb, kbs);
   TRY_OZ(launch_pairs(ozm_kernel, dim3(ntile * mblk, 1, kOzModuli * S), st, mA, mV, M, N, BN, ntile,
@@ -1369,7 +1384,7 @@ int oz_gemm_group(cudaStream_t st, int count, const OzGroupItem* items, DevStatu
   for (int i = 0; i < count; ++i) {
     const OzGroupItem& it = items[i];
     if (it.N <= 0 || it.M <= 0) continue;
-    if (it.kp % MBK != 0 || it.kp > kOzMaxK) return CHASE_ERR_UNSUPPORTED;
+    if (it.kp % MBK != 0 || it.kp > kOzSplitMaxK) return CHASE_ERR_UNSUPPORTED;  // K is not split here
     const int sets = it.c3 ? 3 : 1;  // three-product layout: P1, P2, P3
     if ((size_t)sets * kOzModuli * it.M * it.N > it.resbuf.bytes) return CHASE_ERR_OOM;
     if (P.count + sets > kOzGroupMax || C.count + 1 > kOzGroupMax) TRY_OZ(flush());

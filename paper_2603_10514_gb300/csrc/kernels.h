@@ -121,6 +121,8 @@ constexpr int kOzModuli = 17;                   // residue planes per operand
 constexpr size_t kOzPlaneBytes = 2 * kOzModuli; // bytes of residue planes per operand element
 constexpr int kOzMaxSplits = 2;                 // K splits of one product (residue slabs)
 constexpr int kOzMaxK = 1 << 17;                // longest K the moduli's product covers
+constexpr int kOzSplitMaxK = 1 << 16;           // longest K of one split: |sum| <= 2^16 * 128^2 = 2^30,
+                                                // the range of the modular epilogue's reduction
 // Device bytes of the residue buffer oz_gemm needs for an M x N product.
 size_t oz_residue_bytes(int M, int N);
 template <class T>

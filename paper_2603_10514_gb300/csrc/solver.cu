@@ -1046,7 +1046,10 @@ struct Solve final : SolveBase {
     return rc;
   }
 
-  bool group_filter_ok() const override { return emu && !lowprec && !cfg.graph_filter; }
+  // the grouped launch runs each product's K unsplit (K = n), so longer ones filter alone
+  bool group_filter_ok() const override {
+    return emu && !lowprec && !cfg.graph_filter && n <= kOzSplitMaxK;
+  }
   cudaStream_t stream() const override { return st; }
 
   int group_filter_prepare(GroupFilterItem* g) override {
