@@ -761,8 +761,9 @@ __device__ __forceinline__ long long oz_int(double x, int e) {
 // integers of magnitude <= 128) in plane j.
 __device__ __forceinline__ void write_residues_int(long long X, __nv_bfloat16* base, size_t idx,
                                                    size_t plane) {
-  // |X| as two 30-bit halves: |X| mod p = (U1 (2^29 mod p) + U0) mod p in 32-bit arithmetic
-  // (remainders by compile-time constants)
+  // |X| = U1 2^29 + U0 with U0 < 2^29 and U1 < 2^30: |X| mod p = ((U1 mod p) (2^29 mod p) +
+  // U0 mod p) mod p in 32-bit arithmetic (remainders by compile-time constants; the product
+  // stays below 2^16)
   const unsigned long long U = (unsigned long long)(X < 0 ? -X : X);
   const uint32_t U1 = (uint32_t)(U >> 29), U0 = (uint32_t)(U & ((1u << 29) - 1));
 #pragma unroll
