@@ -304,7 +304,10 @@ int hh_panel_coop(cudaStream_t st, int n, int j0, int b, T* X, int ldx, T* Vh, i
                   Scratch ws, DevStatus* dst, int* launches) {
   static const int per_sm = [] {
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, hh_panel_coop_kernel<T>, 256, 0) != cudaSuccess) v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, hh_panel_coop_kernel<T>, 256, 0) != cudaSuccess) {
+      cudaGetLastError();  // the caller falls back to the per-column panel; no stale error left
+      v = 0;
+    }
     return v;
   }();
   const int m = n - j0;
