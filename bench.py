@@ -710,7 +710,7 @@ def main():
                 "algorithmic_bytes": alg_bytes}
     else:
         # the FP64-accurate products run on the BF16 tensor cores: the method's FP64 work is
-        # set against the BF16 pipe's measured sustained peak (frac), and the BF16 digit
+        # set against the BF16 pipe's measured sustained peak (frac), and the BF16 modular
         # products the kernels actually issue (OZAKI_PAIRS per FP64-equivalent flop; 3 for the
         # BF16x3 filter iterations) give the tensor pipe's own efficiency (frac_tensor_pipe)
         lp = st["filter_flops_lowprec"]

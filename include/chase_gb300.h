@@ -241,8 +241,9 @@ int chase_qr(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int 
  *                   to the FP64 error class (the products chase_solve uses in
  *                   that precision).
  * The Cholesky factor, its inverse and the Householder fallback stay FP64.
- * Other precisions return -9.  Workspace grows by about 16 (2n or n) ncols
- * bytes of digit planes in the emulated mode.
+ * Other precisions return -9.  In the emulated mode the workspace grows by the
+ * products' residue planes, residues and FP64 staging: about 450 n ncols bytes
+ * (complex) or 150 n ncols bytes (real).
  */
 int chase_qr_prec(chase_handle h, chase_dtype dtype, int n, int ncols, void* dX, int ldx,
                   double est_cond, int qr_force, chase_precision prec, int* variant_used,

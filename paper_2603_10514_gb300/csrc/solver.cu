@@ -316,7 +316,7 @@ int filter_mixed(chase_ctx* h, int n, const T* A, int lda, bool split_A, int nco
 }
 
 // ---------------------------------------------------------------------------
-// FP64-accurate A*V products by the Ozaki scheme (gemm_oz.cu): digit planes of
+// FP64-accurate A*V products by the Ozaki scheme II (gemm_oz.cu): residue planes of
 // A (prepared once per call site) and of the current block.
 // ---------------------------------------------------------------------------
 struct OzBufs {
@@ -631,7 +631,7 @@ int oz_gram(chase_ctx* h, OzProd& P, int q, const T* X, int ldx, const T* Y, int
   return 0;
 }
 
-// Digit planes of the small right factor B (kl x N, ld ldb) for oz_tall.  kpk: padded K of
+// Residue planes of the small right factor B (kl x N, ld ldb) for oz_tall.  kpk: padded K of
 // the product (0: the whole block's, P.kpl; a narrower factor passes tc_kpad of its own K so
 // that the modular products do not run over zero padding).
 template <class T>

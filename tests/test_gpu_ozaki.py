@@ -1,10 +1,10 @@
 """FP64-accurate products by the Ozaki scheme on the BF16 tensor cores (CHASE_FP64_EMU),
 through the C ABI.
 
-Tolerances: the emulated product is accurate to ~2^-53 |A||V| per entry (7 digits of
-8 bits = 56 bits of each scaled operand, dropped digit pairs below 2^-56 of the leading
-scale, exact integer accumulation of the leading levels), i.e. the same class as an FP64
-GEMM; the tests hold it to the FP64 tolerances of the parity tests:
+Tolerances: the emulated product is accurate to ~2^-53 |A||V| per entry (each scaled
+operand rounded to a 57-bit integer, the integer product formed exactly from 17 modular
+products and the Chinese remainder theorem, then rounded once to FP64), i.e. the same class
+as an FP64 GEMM; the tests hold it to the FP64 tolerances of the parity tests:
   * one filter step vs FP64 numpy: every entry within the Ozaki bound
     K 2^-53 max_k|A_mk| max_k|V_kc| (plus 2^-52 for the FP64 recurrence terms), and
     dense columns within 1e-13 normwise, as an FP64 product;
