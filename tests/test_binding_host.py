@@ -26,3 +26,33 @@ def test_default_stream_is_passed_as_cuda_stream_legacy(monkeypatch):
     P.Handle(0).close()
     assert fake.streams == [P.CUDA_STREAM_LEGACY, 0x7F00AB, None]
     assert P.CUDA_STREAM_LEGACY == 1
+
+
+def test_missing_library_raises_with_no_fallback(monkeypatch, tmp_path):
+    """Without the built CUDA library every call fails loudly: there is no CPU path."""
+    monkeypatch.setattr(P, "_lib", None)
+    monkeypatch.setattr(P, "LIB_PATH", str(tmp_path / "libchase_gb300.so"))
+    import pytest
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        P.lib()
+    with pytest.raises(RuntimeError):
+        P.Handle(0)
+
+
+def test_product_sources_never_reach_the_oracle():
+    """The package, its CUDA sources and the public header neither import, link nor load the
+    oracle (test infrastructure only)."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pat = re.compile(r"\bimport oracle\b|\bfrom oracle\b|liboracle|chase_oracle|orc_[a-z]")
+    hits = []
+    for d in ("paper_2603_10514_gb300", "include"):
+        for dirpath, dirnames, files in os.walk(os.path.join(root, d)):
+            dirnames[:] = [x for x in dirnames if x not in ("_build", "__pycache__")]
+            for f in files:
+                if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                    text = open(os.path.join(dirpath, f), errors="replace").read()
+                    if pat.search(text):
+                        hits.append(os.path.join(d, f))
+    assert hits == []
