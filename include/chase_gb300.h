@@ -28,6 +28,21 @@
  *     positive values are the chase_status codes below.
  *   - No entry point traps or aborts: device-side failures (a non-positive
  *     Cholesky pivot, a non-finite value) are reported through status codes.
+ *
+ * Minimal use (dA: n x n Hermitian, dV: n x (nev + nex) start block, both on
+ * device 0; error checks left out):
+ *
+ *   chase_handle h;
+ *   chase_create(&h, 0, NULL);                  // the handle makes its own stream
+ *   chase_config cfg;
+ *   chase_config_default(&cfg);
+ *   cfg.opt_degree = 1;                         // per-column degrees
+ *   cfg.prec = CHASE_FP64_EMU;                  // FP64-accurate tensor-core products
+ *   chase_stats st;
+ *   int rc = chase_solve(h, CHASE_C128, n, dA, n, nev, nex, &cfg, NULL, dV, n,
+ *                        evals, resid, &st, NULL, 0);   // bounds by Lanczos
+ *   // rc == CHASE_OK: evals[0..nev) ascending, dV's first nev columns the vectors
+ *   chase_destroy(h);
  */
 #ifndef CHASE_GB300_H
 #define CHASE_GB300_H

@@ -55,6 +55,24 @@ def test_header_compiles_as_c(tmp_path):
                     str(src), "-o", str(tmp_path / "t.o")], check=True)
 
 
+def test_documented_minimal_use_compiles_as_c(tmp_path):
+    """The usage example in the header's introduction is valid C against the header."""
+    lines = open(os.path.join(ROOT, "include", "chase_gb300.h")).read().splitlines()
+    start = next(i for i, t in enumerate(lines) if "Minimal use" in t)
+    body = []
+    for t in lines[start + 1:]:
+        if t.strip() == "*/":
+            break
+        body.append(t.strip()[1:].strip() if t.strip().startswith("*") else t)
+    code = "\n".join(x for x in body if x and not x.startswith("device 0"))
+    src = tmp_path / "use.c"
+    src.write_text('#include "chase_gb300.h"\n'
+                   "int use(int n, const void* dA, void* dV, int nev, int nex, double* evals,\n"
+                   "        double* resid) {\n" + code + "\n  return rc;\n}\n")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-c", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(tmp_path / "use.o")], check=True)
+
+
 def test_config_defaults(cl):
     cfg = cl.config_default()
     assert cfg.tol == 1e-10 and cfg.deg_init == 20 and cfg.deg_max == 36
